@@ -1,0 +1,517 @@
+"""Pins of the FP64 CPU oracle to facts fixed by the paper and by the mathematics.
+
+None of these compares the oracle with itself: each checks a printed value, a
+closed-form solution, an exact identity of the scheme, or a brute-force
+restatement on a tiny mesh.  Together they are chosen so that a dropped term,
+a wrong sign, a wrong index or a transposed operand anywhere in the oracle
+fails at least one of them.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_1812_00390_gb300 import meshgen as mg
+from paper_1812_00390_gb300.meshgen import BC, BC_INLET, BC_OUTLET, BC_PERIODIC, BC_SYMMETRY, BC_WALL
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _lattice_golden():
+    rows = []
+    with open(os.path.join(GOLDEN, "d2q9_lattice.txt")) as fh:
+        for line in fh:
+            line = line.split("#")[0].split()
+            if line:
+                rows.append((int(line[1]), int(line[2]), float(Fraction(line[3]))))
+    return np.array(rows)
+
+
+def _feq_all(orc, rho, u):
+    return np.array([orc.feq(float(r), float(x), float(y)) for r, (x, y) in zip(rho, u)])
+
+
+# --------------------------------------------------------------------------- lattice
+def test_lattice_matches_paper(orc):
+    """Weights and velocities of Sec. 2.1 (golden fixture): f^eq(1, 0) = w and
+    d f^eq / d u at u = 0 equals w e / c_s^2."""
+    g = _lattice_golden()
+    w = orc.feq(1.0, 0.0, 0.0)
+    np.testing.assert_allclose(w, g[:, 2], rtol=0, atol=1e-16)
+    eps = 1e-3
+    ex = (orc.feq(1.0, eps, 0.0) - orc.feq(1.0, -eps, 0.0)) / (2 * eps) / (3 * g[:, 2])
+    ey = (orc.feq(1.0, 0.0, eps) - orc.feq(1.0, 0.0, -eps)) / (2 * eps) / (3 * g[:, 2])
+    np.testing.assert_allclose(ex, g[:, 0], atol=1e-12)
+    np.testing.assert_allclose(ey, g[:, 1], atol=1e-12)
+
+
+def test_equilibrium_moments(orc):
+    """Eq. (feq) reproduces rho, rho u and rho (u u + c_s^2 I) exactly (Sec. 2.1)."""
+    g = _lattice_golden()
+    e = g[:, :2]
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        rho = 1 + 0.2 * rng.uniform(-1, 1)
+        u = 0.2 * rng.uniform(-1, 1, 2)
+        f = orc.feq(rho, *u)
+        assert abs(f.sum() - rho) < 1e-15
+        np.testing.assert_allclose(f @ e, rho * u, atol=1e-15)
+        P = np.einsum("a,ai,aj->ij", f, e, e)
+        np.testing.assert_allclose(P, rho * (np.outer(u, u) + np.eye(2) / 3), atol=1e-15)
+
+
+# --------------------------------------------------------------------------- geometry / dt
+def test_geometry_and_cfl_dt(orc):
+    """Right triangles of legs h: A = h^2/2, centroid = vertex mean, and the CFL
+    rule of Eqs. (CFL), (timetau) gives dt = CFL (h/4) / (sqrt2 + U), capped at 2 tau."""
+    h = 0.5
+    m = mg.couette(nx=4, ny=3, h=h, jitter=0.0)
+    o = orc.Oracle(m)
+    a, c, l = o.geometry()
+    np.testing.assert_allclose(a, h * h / 2, rtol=1e-15)
+    for k in range(m.n_cell):
+        v = m.cell_vert[m.cell_ptr[k]:m.cell_ptr[k + 1]]
+        np.testing.assert_allclose(c[k], m.xy[v].mean(0), atol=1e-15)
+    np.testing.assert_allclose(l, h, rtol=1e-15)
+    assert abs(o.cfl_dt(0.5, 0.1, 10.0, "euler") - 0.5 * (h / 4) / (np.sqrt(2) + 0.1)) < 1e-15
+    assert o.cfl_dt(0.5, 0.1, 1e-3, "euler") == 2e-3
+    assert o.cfl_dt(0.5, 0.1, 1e-3, "ab2") == 1e-3
+    # quads of a stretched cavity: shoelace area sums to the domain area
+    mq = mg.cavity(8, ratio=5.0)
+    aq, cq, _ = orc.Oracle(mq).geometry()
+    assert abs(aq.sum() - 1.0) < 1e-14
+    # quad centroid of an axis-aligned rectangle is its centre
+    xs = mg.tanh_nodes(8, 5.0)
+    np.testing.assert_allclose(cq[0], [(xs[0] + xs[1]) / 2, (xs[0] + xs[1]) / 2], atol=1e-15)
+
+
+def test_mesh_validation(orc):
+    m = mg.couette(nx=4, ny=2)
+    bad = mg.Mesh(m.xy, m.cell_ptr, m.cell_vert, m.bedge[:-1], m.btag[:-1], m.bcs)
+    with pytest.raises(ValueError, match="untagged"):
+        orc.Oracle(bad)
+    cw = mg.Mesh(m.xy, m.cell_ptr, m.cell_vert[::-1].copy(), m.bedge, m.btag, m.bcs)
+    with pytest.raises(ValueError):
+        orc.Oracle(cw)
+
+
+# --------------------------------------------------------------------------- collision / time
+@pytest.mark.parametrize("scheme", ["euler", "rk2", "rk4", "ab2"])
+def test_uniform_relaxation_closed_form(orc, scheme):
+    """A spatially uniform, non-equilibrium state on a fully periodic mesh has zero
+    flux; rho, u are collision invariants, so f - f^eq obeys the scalar linear ODE
+    y' = -y/tau, whose discrete solution for each scheme of Sec. 2.3 is known
+    exactly: Euler (1-z)^n, midpoint RK2 (1-z+z^2/2)^n, 4-stage RK with beta =
+    (1/4,1/3,1/2,1) the 4th-order Taylor polynomial, AB2 its two-step recurrence
+    started by one Euler step."""
+    # cells large enough that dt = 0.3 is within the CFL limit (rounding noise
+    # on top of the uniform state must not grow)
+    m = mg.periodic_tri(nx=6, ny=5, lx=30.0, ly=25.0, jitter=0.2, seed=4)
+    o = orc.Oracle(m)
+    rng = np.random.default_rng(1)
+    f0 = orc.feq(1.02, 0.03, -0.02) + 2e-3 * rng.uniform(-1, 1, 9)
+    rho = f0.sum()
+    g = _lattice_golden()
+    u = (f0 @ g[:, :2]) / rho
+    fe = orc.feq(rho, *u)
+    tau, dt, n = 0.7, 0.3, 12
+    z = dt / tau
+    o.set_f(np.tile(f0, (m.n_cell, 1)))
+    o.run(scheme, tau, dt, n)
+    if scheme == "euler":
+        amp = (1 - z) ** n
+    elif scheme == "rk2":
+        amp = (1 - z + z * z / 2) ** n
+    elif scheme == "rk4":
+        amp = (1 - z + z ** 2 / 2 - z ** 3 / 6 + z ** 4 / 24) ** n
+    else:
+        y = [1.0, 1.0 - z]
+        for _ in range(n - 1):
+            y.append(y[-1] + 0.5 * z * (-3 * y[-1] + y[-2]))
+        amp = y[n]
+    expect = fe + amp * (f0 - fe)
+    np.testing.assert_allclose(o.get_f(), np.tile(expect, (m.n_cell, 1)), rtol=0, atol=1e-14)
+
+
+# --------------------------------------------------------------------------- advection operator
+def _interior_cells(m, depth):
+    """Cells whose `depth`-ring of face neighbours holds no boundary face."""
+    edges = {}
+    for c in range(m.n_cell):
+        v = m.cell_vert[m.cell_ptr[c]:m.cell_ptr[c + 1]]
+        for k in range(len(v)):
+            key = tuple(sorted((int(v[k]), int(v[(k + 1) % len(v)]))))
+            edges.setdefault(key, []).append(c)
+    nb = [[] for _ in range(m.n_cell)]
+    bad = set()
+    for cells in edges.values():
+        if len(cells) == 2:
+            nb[cells[0]].append(cells[1]); nb[cells[1]].append(cells[0])
+        else:
+            bad.add(cells[0])
+    for _ in range(depth):
+        bad = bad | {j for c in bad for j in nb[c]}
+    return np.array([c for c in range(m.n_cell) if c not in bad])
+
+
+@pytest.mark.parametrize("mesh", ["tri", "quad", "hybrid"])
+def test_linear_field_exactness(orc, mesh):
+    """For f_alpha linear in x, the least-squares gradient (Eq. leastsquare) is
+    exact, so is the upwind face value (Eq. lslrflux), and the midpoint flux sum
+    of Eq. (rhs) equals A e.grad f exactly: RHS = -e_alpha . b_alpha on every cell
+    whose 2-ring is interior (collision switched off with tau -> inf)."""
+    if mesh == "tri":
+        m = mg.channel(nx=14, ny=10, lx=1.4, ly=1.0, jitter=0.2, seed=8)
+    elif mesh == "quad":
+        m = mg.cavity(12, ratio=4.0)
+    else:
+        m = mg.cylinder_hybrid(n_rad=6, n_circ=24, first=0.05, growth=1.2, r_far=6.0,
+                               n_tri_rings=6, seed=3)
+    o = orc.Oracle(m)
+    _, c, _ = o.geometry()
+    rng = np.random.default_rng(5)
+    a0 = rng.uniform(0.1, 0.5, 9)
+    b = rng.uniform(-0.2, 0.2, (9, 2))
+    f = a0[None, :] + c @ b.T
+    r = o.rhs(f, 1e300)
+    inner = _interior_cells(m, 2)
+    assert len(inner) > 10
+    g = _lattice_golden()
+    expect = -(g[:, :2] * b).sum(1)
+    np.testing.assert_allclose(r[inner], np.tile(expect, (len(inner), 1)), rtol=0, atol=1e-13)
+
+
+def test_two_cell_brute_force(orc):
+    """Two triangles (unit square, moving lid): the RHS restated from the paper's
+    equations with the gradient found by a direct weighted least-squares solve
+    (numpy lstsq, not normal equations) agrees with the oracle to rounding."""
+    g = _lattice_golden()
+    e, w = g[:, :2], g[:, 2]
+    m = mg.two_triangles(lid=0.1)
+    o = orc.Oracle(m)
+    rng = np.random.default_rng(12)
+    f = np.array([orc.feq(1 + 0.05 * rng.uniform(-1, 1), *(0.05 * rng.uniform(-1, 1, 2)))
+                  + 1e-3 * rng.uniform(0, 1, 9) for _ in range(2)])
+    tau = 0.37
+    xy = m.xy
+
+    def feq(rho, u):
+        eu = e @ u
+        return rho * w * (1 + 3 * eu + 4.5 * eu ** 2 - 1.5 * u @ u)
+
+    cells = [m.cell_vert[m.cell_ptr[k]:m.cell_ptr[k + 1]] for k in range(2)]
+    cen = [xy[v].mean(0) for v in cells]
+    area = [0.5, 0.5]
+    lid = {(2, 3)}
+    rho = f.sum(1)
+    u = (f @ e) / rho[:, None]
+    feq_c = [feq(rho[k], u[k]) for k in range(2)]
+
+    def fP(k, top):
+        uw = np.array([0.1, 0.0]) if top else np.zeros(2)
+        return feq(rho[k], uw) + f[k] - feq_c[k]
+
+    grads, faces = [], []
+    for k in range(2):
+        v = cells[k]
+        rows, rhs, fl = [], [], []
+        for s in range(3):
+            a_, b_ = int(v[s]), int(v[(s + 1) % 3])
+            mid = (xy[a_] + xy[b_]) / 2
+            N = np.array([xy[b_, 1] - xy[a_, 1], -(xy[b_, 0] - xy[a_, 0])])
+            if {a_, b_} == {0, 2}:
+                pt, val, kind = cen[1 - k], f[1 - k], "in"
+            else:
+                pt, val, kind = mid, fP(k, tuple(sorted((a_, b_))) in lid), "wall"
+            d = pt - cen[k]
+            sw = 1 / np.linalg.norm(d)
+            rows.append(sw * d)
+            rhs.append(sw * (val - f[k]))
+            fl.append((N, mid, kind, val))
+        G = np.linalg.lstsq(np.array(rows), np.array(rhs), rcond=None)[0]  # [2, 9]
+        grads.append(G)
+        faces.append(fl)
+    out = np.zeros((2, 9))
+    for k in range(2):
+        flux = np.zeros(9)
+        for N, mid, kind, val in faces[k]:
+            en = e @ N
+            if kind == "wall":
+                fv = val
+            else:
+                j = 1 - k
+                own = f[k] + (mid - cen[k]) @ grads[k]
+                other = f[j] + (mid - cen[j]) @ grads[j]
+                fv = np.where(en > 0, own, other)
+            flux += en * fv
+        out[k] = -flux / area[k] - (f[k] - feq_c[k]) / tau
+    np.testing.assert_allclose(o.rhs(f, tau), out, rtol=0, atol=2e-15)
+
+
+# --------------------------------------------------------------------------- invariants
+@pytest.mark.parametrize("case", ["periodic", "cavity_rest"])
+def test_equilibrium_fixed_point(orc, case):
+    """Uniform equilibrium is a fixed point: on a fully periodic jittered mesh with
+    uniform rho, u; in a closed cavity at rest with every wall at rest."""
+    if case == "periodic":
+        m = mg.periodic_tri(nx=10, ny=8, lx=10.0, ly=8.0, jitter=0.2, seed=6)
+        rho, u = 1.03, (0.04, -0.03)
+    else:
+        m = mg.cavity(10, ratio=6.0, U=0.0)
+        rho, u = 1.0, (0.0, 0.0)
+    o = orc.Oracle(m)
+    o.set_equilibrium(rho, u)
+    f0 = o.get_f()
+    o.run("rk2", 0.2, o.cfl_dt(0.5, 0.05, 0.2, "rk2"), 50)
+    np.testing.assert_allclose(o.get_f(), f0, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("case", ["couette", "cavity", "periodic"])
+def test_mass_conservation(orc, case):
+    """Closed or periodic domains conserve sum(A rho) exactly: interior fluxes are
+    antisymmetric, a wall moving tangentially carries no mass (Eq. wallbc), and
+    collision conserves rho (Eq. feq)."""
+    if case == "couette":
+        m = mg.couette(nx=16, ny=6)
+    elif case == "cavity":
+        m = mg.cavity(12, ratio=8.0)
+    else:
+        m = mg.periodic_quad(nx=9, ny=7, jitter=0.15)
+    o = orc.Oracle(m)
+    rho, u, dev = mg.random_state(m.n_cell, seed=3)
+    f = _feq_all(orc, rho, u) + dev * 0.1
+    o.set_f(f)
+    m0 = o.mass()
+    o.run("euler", 0.3, o.cfl_dt(0.5, 0.1, 0.3, "euler"), 200)
+    assert abs(o.mass() - m0) / m0 < 200 * 1e-15
+
+
+def test_symmetry_plane_carries_no_mass(orc):
+    """A symmetry face (Sec. 2.4) is impermeable: with u* the mirror image of u_i,
+    sum_alpha (e.n) (f_i + f_GC)/2 = rho (u_i + u*).n / 2 = 0, so a box closed by
+    walls and symmetry planes conserves mass exactly from any state."""
+    m = mg.cavity(10, ratio=3.0)
+    ym = m.xy[m.bedge, 1].mean(1)
+    bt = np.where(np.abs(ym) < 1e-12, 1, 0).astype(np.int32)      # bottom: symmetry
+    xm = m.xy[m.bedge, 0].mean(1)
+    bt[np.abs(xm - 1.0) < 1e-12] = 1                             # right: symmetry
+    m.btag = bt
+    m.bcs = [BC(BC_WALL), BC(BC_SYMMETRY)]
+    o = orc.Oracle(m)
+    rho, u, dev = mg.random_state(m.n_cell, seed=21)
+    o.set_f(_feq_all(orc, rho, u) + 0.1 * dev)
+    m0 = o.mass()
+    o.run("rk2", 0.2, o.cfl_dt(0.5, 0.1, 0.2, "rk2"), 100)
+    assert abs(o.mass() - m0) / m0 < 100 * 1e-15
+
+
+def test_stencil_point_geometry(orc):
+    """Least-squares stencil points: neighbour centroid, neighbour centroid moved by
+    the period vector across a periodic face, wall-face midpoint P (Eq. wallbc),
+    and for inlet / outlet / symmetry faces the mirror image of the cell centroid
+    in the face line (equidistant from the face, on its normal)."""
+    m = mg.couette(nx=6, ny=3, jitter=0.15)
+    o = orc.Oracle(m)
+    _, c, _ = o.geometry()
+    seen = set()
+    for k in range(m.n_cell):
+        v = m.cell_vert[m.cell_ptr[k]:m.cell_ptr[k + 1]]
+        for s in range(len(v)):
+            kind, p = o.stencil_point(k, s)
+            a_, b_ = m.xy[v[s]], m.xy[v[(s + 1) % len(v)]]
+            seen.add(kind)
+            if kind == BC_WALL:
+                np.testing.assert_allclose(p, (a_ + b_) / 2, atol=1e-15)
+            elif kind == 11:      # periodic image sits next to the cell, not a period away
+                assert np.linalg.norm(p - c[k]) < 1.5 and min(c[k, 0], 6.0 - c[k, 0]) < 1.0
+    assert seen == {BC_WALL, 10, 11}
+    mc = mg.channel(nx=6, ny=4, jitter=0.2, top_bottom="symmetry")
+    o = orc.Oracle(mc)
+    _, c, _ = o.geometry()
+    n_ghost = 0
+    for k in range(mc.n_cell):
+        v = mc.cell_vert[mc.cell_ptr[k]:mc.cell_ptr[k + 1]]
+        for s in range(len(v)):
+            kind, p = o.stencil_point(k, s)
+            if kind in (BC_INLET, BC_OUTLET, BC_SYMMETRY):
+                a_, b_ = mc.xy[v[s]], mc.xy[v[(s + 1) % len(v)]]
+                t = (b_ - a_) / np.linalg.norm(b_ - a_)
+                mid = (p + c[k]) / 2
+                assert abs(t[0] * (mid - a_)[1] - t[1] * (mid - a_)[0]) < 1e-14   # midpoint on the face line
+                assert abs(np.dot(t, p - c[k])) < 1e-14            # along the normal
+                n_ghost += 1
+    assert n_ghost == 2 * 6 + 2 * 4
+
+
+# --------------------------------------------------------------------------- closed forms
+def _couette_series(y, t, U, H, nu, K=400):
+    u = U * y / H
+    for k in range(1, K):
+        u += 2 * U * (-1) ** k / (k * np.pi) * np.sin(k * np.pi * y / H) * np.exp(-(k * np.pi) ** 2 * nu * t / H ** 2)
+    return u
+
+
+def test_couette_unsteady_series(orc):
+    """Plate-driven Couette flow (Sec. 3.1) from rest against the diffusion-equation
+    series with nu = tau c_s^2 (Eq. relaxtime, no 1/2 shift): the 32x8 jittered
+    channel, Re = 10, lid 0.1, 2000 explicit-Euler steps.  Measured O(h^2) error
+    3.3e-4; a 10% error in nu moves the profile by ~1.7e-3."""
+    m = mg.couette()
+    o = orc.Oracle(m)
+    _, c, _ = o.geometry()
+    tau = 3 * 0.1 * 8 / 10
+    dt = o.cfl_dt(0.5, 0.1, tau, "euler")
+    o.set_equilibrium(1.0, (0.0, 0.0))
+    o.run("euler", tau, dt, 2000)
+    _, u = o.macros()
+    err = np.abs(u[:, 0] - _couette_series(c[:, 1], 2000 * dt, 0.1, 8.0, tau / 3)).max()
+    assert err < 6e-4
+    assert np.abs(u[:, 1]).max() < 2e-4
+
+
+def test_couette_spatial_order(orc):
+    """Second-order spatial accuracy (Sec. 3.1): L2 error of the unsteady Couette
+    profile at fixed time falls at least as h^1.8 from 4 to 16 rows."""
+    H, tau, T = 8.0, 0.24, 40.0
+    errs = []
+    for ny in (4, 16):
+        m = mg.couette(nx=2 * ny, ny=ny, h=H / ny, jitter=0.1, seed=5)
+        o = orc.Oracle(m)
+        a, c, _ = o.geometry()
+        dt = min(o.cfl_dt(0.5, 0.1, tau, "rk2"), 0.05)
+        n = int(round(T / dt))
+        o.set_equilibrium(1.0, (0.0, 0.0))
+        o.run("rk2", tau, T / n, n)
+        _, u = o.macros()
+        e = u[:, 0] - _couette_series(c[:, 1], T, 0.1, H, tau / 3)
+        errs.append(np.sqrt((a * e * e).sum() / a.sum()))
+    order = np.log2(errs[0] / errs[1]) / 2
+    assert order > 1.8, (errs, order)
+
+
+def test_shear_wave_decay(orc):
+    """A sinusoidal shear wave on a fully periodic jittered mesh decays as
+    exp(-nu k^2 t) with nu = tau/3 (Eq. relaxtime): decay rate within 3%."""
+    L, U, tau = 32.0, 0.05, 0.3
+    k = 2 * np.pi / L
+    m = mg.periodic_tri(nx=16, ny=16, lx=L, ly=L, jitter=0.15, seed=2)
+    o = orc.Oracle(m)
+    a, c, _ = o.geometry()
+    u0 = np.zeros((m.n_cell, 2))
+    u0[:, 0] = U * np.sin(k * c[:, 1])
+    o.set_equilibrium(np.ones(m.n_cell), u0)
+    amps = []
+    for _ in range(2):
+        o.run("rk2", tau, 0.1, 1000)
+        _, u = o.macros()
+        amps.append(2 * (a * u[:, 0] * np.sin(k * c[:, 1])).sum() / a.sum())
+    rate = np.log(amps[0] / amps[1]) / 100.0
+    assert abs(rate / (tau / 3 * k * k) - 1) < 0.03
+
+
+def test_far_field_free_stream(orc):
+    """External inlet (rho* = rho_inf) and outlet (f_GC = f_i) of Sec. 2.4: a box
+    with inlets left/top/bottom and an outlet right, started at rest, relaxes to
+    the uniform free stream u_inf."""
+    m = mg.channel(nx=24, ny=12, lx=2.0, ly=1.0, u_inf=(0.05, 0.0), top_bottom="inlet")
+    o = orc.Oracle(m)
+    tau = 0.01
+    o.set_equilibrium(1.0, (0.0, 0.0))
+    o.run("euler", tau, o.cfl_dt(0.5, 0.05, tau, "euler"), 8000)
+    rho, u = o.macros()
+    assert np.abs(u[:, 0] - 0.05).max() < 2e-4
+    assert np.abs(u[:, 1]).max() < 1e-4
+    assert np.abs(rho - 1).max() < 2e-4
+
+
+def test_symmetry_plane_stokes_layer(orc):
+    """Symmetry face (Sec. 2.4, u* = (u, -v) on a horizontal face) over a wall
+    moving at U: the flow from rest is the half of a channel with both walls
+    moving, u = U - sum 4U/((2k+1)pi) sin(l_k y) exp(-l_k^2 nu t),
+    l_k = (2k+1) pi / (2H); within 2.5% of U."""
+    m = mg.couette(nx=16, ny=8, h=1.0, U=0.1, jitter=0.1, seed=9)
+    m.bcs[0] = BC(BC_WALL, u_w=(0.1, 0.0))
+    m.bcs[2] = BC(BC_SYMMETRY)
+    o = orc.Oracle(m)
+    _, c, _ = o.geometry()
+    H, U, tau = 8.0, 0.1, 0.24
+    nu = tau / 3
+    o.set_equilibrium(1.0, (0.0, 0.0))
+    o.run("rk2", tau, 0.05, 2000)
+    t = 100.0
+    y = c[:, 1]
+    ex = U * np.ones_like(y)
+    for k in range(200):
+        lam = (2 * k + 1) * np.pi / (2 * H)
+        ex -= 4 * U / ((2 * k + 1) * np.pi) * np.sin(lam * y) * np.exp(-lam * lam * nu * t)
+    _, u = o.macros()
+    assert np.abs(u[:, 0] - ex).max() < 2.5e-3
+
+
+def test_internal_inlet_outlet_poiseuille(orc):
+    """Internal velocity inlet (rho* = rho_i) and pressure outlet
+    (f^eq(rho_inf, u_i) + f_i - f^eq_i) of Sec. 2.4 between two walls: the steady
+    flow is Poiseuille flow -- umax/umean = 3/2, constant mass flux rho_in u_inf,
+    linear pressure drop dp/dx = -12 nu (mass flux) / H^3, and rho -> rho_inf at the
+    outlet."""
+    nx, ny, H, Lx = 60, 12, 1.0, 5.0
+    m = mg.channel(nx=nx, ny=ny, lx=Lx, ly=H, u_inf=(0.05, 0.0), top_bottom="inlet",
+                   external=0, jitter=0.1)
+    ym = m.xy[m.bedge, 1].mean(1)
+    bt = m.btag.copy()
+    bt[(np.abs(ym) < 1e-12) | (np.abs(ym - H) < 1e-12)] = 2
+    m.btag = bt
+    m.bcs = [BC(BC_INLET, external=0, u_inf=(0.05, 0.0)), BC(BC_OUTLET, external=0, rho_inf=1.0),
+             BC(BC_WALL)]
+    o = orc.Oracle(m)
+    _, c, _ = o.geometry()
+    tau = 0.03
+    o.set_equilibrium(1.0, (0.0, 0.0))
+    o.run("euler", tau, o.cfl_dt(0.5, 0.075, tau, "euler"), 20000)
+    rho, u = o.macros()
+    fluxes, rhos = [], []
+    for x0 in (1.5, 2.5, 3.5):
+        sel = np.abs(c[:, 0] - x0) < 0.2
+        y = c[sel, 1]
+        i = np.argsort(y)
+        q = np.trapezoid(np.r_[0, (rho[sel] * u[sel, 0])[i], 0], np.r_[0, y[i], H])
+        rm = rho[sel].mean()
+        fluxes.append(q)
+        rhos.append(rm)
+        assert abs(u[sel, 0].max() / (q / H / rm) - 1.5) < 0.05
+    inlet = np.abs(c[:, 0]) < 0.15
+    np.testing.assert_allclose(fluxes, fluxes[0], rtol=0.01)
+    assert abs(fluxes[0] / (rho[inlet].mean() * 0.05) - 1) < 0.03
+    dpdx = (rhos[-1] - rhos[0]) / 3 / 2.0        # p = rho / 3, over 2 length units
+    assert abs(dpdx / (-12 * (tau / 3) * np.mean(fluxes) / H ** 3) - 1) < 0.1
+    outlet = c[:, 0] > Lx - 0.1
+    assert abs(rho[outlet].mean() - 1.0) < 3e-3
+
+
+def test_permutation_invariance(orc):
+    """Cell numbering does not change the solution."""
+    m = mg.cavity(8, ratio=4.0)
+    perm = np.random.default_rng(2).permutation(m.n_cell)
+    mp = m.permuted(perm)
+    o1, o2 = orc.Oracle(m), orc.Oracle(mp)
+    rho, u, dev = mg.random_state(m.n_cell, seed=9)
+    f = _feq_all(orc, rho, u) + 0.1 * dev
+    o1.set_f(f)
+    o2.set_f(f[perm])
+    o1.run("rk2", 0.2, 0.01, 30)
+    o2.run("rk2", 0.2, 0.01, 30)
+    np.testing.assert_allclose(o2.get_f(), o1.get_f()[perm], rtol=0, atol=1e-15)
+
+
+def test_velocity_residual_definition(orc):
+    """Residual of Sec. 3.2: sqrt(sum |u_new - u_old|^2) / sqrt(sum |u_old|^2);
+    zero for an unchanged state, scale-free, and +inf for a start from rest."""
+    m = mg.cavity(6, ratio=3.0)
+    o = orc.Oracle(m)
+    rho, u, _ = mg.random_state(m.n_cell, seed=4)
+    o.set_equilibrium(rho, u)
+    _, un = o.macros()
+    assert o.residual(un) == 0.0
+    assert abs(o.residual(un * 2.0) - 0.5) < 1e-15     # |u - 2u| / |2u|
+    assert o.residual(np.zeros_like(un)) == np.inf
