@@ -1,0 +1,238 @@
+/*
+ * fvlbm.h -- C ABI of the GB300 finite-volume lattice Boltzmann library.
+ *
+ * The library advances the D2Q9 discrete Boltzmann-BGK equation on an
+ * unstructured 2-D mesh of convex polygons with the cell-centred finite-volume
+ * scheme of Wang, Zhong, Cao & Zhuo, "A simplified finite volume lattice
+ * Boltzmann method ... Part I" (arXiv:1812.00390):
+ *
+ *   d f_a / dt = -(1/A) sum_m (e_a . n_m) f_a,m dl_m - (f_a - f_a^eq) / tau
+ *                                                         (Sec. 2.2, Eq. rhs)
+ *
+ * with face values from the least-squares linear upwind reconstruction
+ * (Eq. lslrflux, Eq. leastsquare), the boundary treatment of Sec. 2.4
+ * (Guo extrapolation at walls, Eq. wallbc; ghost values at inlets, outlets and
+ * symmetry planes) and an explicit time scheme (Sec. 2.3).  Every step runs in
+ * CUDA kernels for sm_103a; the host side only builds the mesh, packs it and
+ * launches.
+ *
+ * Conventions for every function below:
+ *  - Return value: FVLBM_OK (0) or a negative fvlbm_status.  No function
+ *    aborts, throws or exits.  fvlbm_last_error() gives a message for the last
+ *    failure on the calling thread.
+ *  - Pointers marked "host" are plain host memory read (or written) during the
+ *    call only; the library copies what it keeps.  The caller keeps ownership.
+ *  - Handles are opaque and owned by the library until the matching
+ *    *_destroy call.
+ *  - Cells are numbered by the caller (0 .. n_cell-1 in the order given to
+ *    fvlbm_mesh_create); every array exchanged with the caller uses that order.
+ *    Internally the library renumbers cells for locality.
+ *  - Distribution functions are indexed a = 0..8 with the D2Q9 velocities of
+ *    Sec. 2.1: e_0 = (0,0); e_1..e_4 = (1,0),(0,1),(-1,0),(0,-1);
+ *    e_5..e_8 = (1,1),(-1,1),(-1,-1),(1,-1); c = 1, c_s^2 = 1/3.
+ */
+#ifndef FVLBM_H
+#define FVLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FVLBM_Q 9
+#define FVLBM_MAX_POLY 8 /* most vertices (and faces) per cell */
+
+typedef enum fvlbm_status {
+    FVLBM_OK = 0,
+    FVLBM_ERR_ARG = -1,               /* bad argument (null pointer, size, enum) */
+    FVLBM_ERR_MESH_TOPOLOGY = -2,     /* edge shared by >2 cells, unmatched periodic edge, ... */
+    FVLBM_ERR_DEGENERATE_CELL = -3,   /* non-positive area, or singular least-squares matrix */
+    FVLBM_ERR_UNTAGGED_BOUNDARY = -4, /* an edge of one cell only that no boundary edge names */
+    FVLBM_ERR_UNSTABLE_DT = -5,       /* dt above 2 tau (Eq. timetau; tau for AB2) or CFL > 1 */
+    FVLBM_ERR_OOM = -6,               /* host or device allocation failed, or workspace too small */
+    FVLBM_ERR_CUDA = -7,              /* a CUDA runtime call failed */
+    FVLBM_ERR_DIVERGED = -8,          /* a non-finite value appeared in the state */
+    FVLBM_ERR_TIMEOUT = -9,           /* a bounded wait ran out */
+    FVLBM_ERR_UNSUPPORTED = -10       /* combination not built (e.g. no GPU) */
+} fvlbm_status;
+
+/* Boundary-condition kinds (Sec. 2.4; periodic as in the Couette case, Sec. 3.1). */
+typedef enum fvlbm_bc_kind {
+    FVLBM_BC_WALL = 0,     /* no-slip wall moving at u_w, Eq. (wallbc) */
+    FVLBM_BC_INLET = 1,    /* ghost f^eq(rho*, u_inf) + f_k - f^eq_k; upwind face value */
+    FVLBM_BC_OUTLET = 2,   /* external: f_GC = f_P = f_i; internal: pressure outlet */
+    FVLBM_BC_SYMMETRY = 3, /* ghost f^eq(rho_i, u mirrored); face value (f_i + f_GC)/2 */
+    FVLBM_BC_PERIODIC = 4  /* edge pairs with the partner tag's edges */
+} fvlbm_bc_kind;
+
+typedef enum fvlbm_scheme {
+    FVLBM_EULER = 0, /* f^{n+1} = f^n + dt RHS^n, Eq. (euler) */
+    FVLBM_RK2 = 1,   /* 2-stage member of the multistage scheme, beta = (1/2, 1) */
+    FVLBM_AB2 = 2,   /* Adams-Bashforth, first step Euler (Sec. 2.3) */
+    FVLBM_RK4 = 3    /* 4-stage scheme, beta = (1/4, 1/3, 1/2, 1) (Sec. 2.3) */
+} fvlbm_scheme;
+
+typedef enum fvlbm_precision {
+    FVLBM_FP64 = 0,     /* f stored and computed in FP64 */
+    FVLBM_FP32_DEV = 1, /* g = f - w stored and computed in FP32 */
+    FVLBM_FP16_DEV = 2, /* g stored in FP16 with a power-of-two scale per (instance, a); FP32 math */
+    FVLBM_BF16_DEV = 3  /* g stored in BF16; FP32 math */
+} fvlbm_precision;
+
+/* One boundary tag.  Boundary edge i uses bcs[btag[i]]. */
+typedef struct fvlbm_bc {
+    int32_t kind;      /* fvlbm_bc_kind */
+    int32_t external;  /* 1: external-flow rules (inlet rho* = rho_inf, outlet f_GC = f_i);
+                          0: internal-flow rules (inlet rho* = rho_i, pressure outlet) */
+    double u_w[2];     /* wall velocity (FVLBM_BC_WALL); must be tangential to the wall */
+    double rho_inf;    /* free-stream density (inlet / outlet) */
+    double u_inf[2];   /* free-stream velocity (inlet / outlet) */
+    int32_t partner;   /* FVLBM_BC_PERIODIC: tag of the matching boundary */
+    int32_t reserved;  /* set to 0 */
+    double shift[2];   /* FVLBM_BC_PERIODIC: partner edge points + shift = this edge's points */
+} fvlbm_bc;
+
+/* Solver parameters, one set per instance (see fvlbm_init). */
+typedef struct fvlbm_params {
+    double tau;        /* relaxation time, tau = nu / c_s^2 = 3 nu (Eq. relaxtime, no +1/2) */
+    double dt;         /* time step; 0 = choose from Eqs. (CFL) and (timetau) */
+    double cfl;        /* CFL number used when dt == 0 (0 = 0.5) */
+    double u_max;      /* |U|_max of Eq. (CFL); 0 = largest boundary / initial speed */
+    int32_t scheme;    /* fvlbm_scheme; equal for all instances of a solver */
+    int32_t precision; /* fvlbm_precision; equal for all instances of a solver */
+    double rho0;       /* initial density (Step 0: f = f^eq(rho0, u0)) */
+    double u0[2];      /* initial velocity */
+    int32_t device;    /* CUDA device ordinal; equal for all instances */
+    int32_t reserved;  /* set to 0 */
+} fvlbm_params;
+
+typedef struct fvlbm_mesh_info_s {
+    int64_t n_cell;        /* cells */
+    int64_t n_face;        /* unique faces (interior + periodic pairs + boundary) */
+    int64_t n_bface;       /* boundary faces (walls, inlets, outlets, symmetry) */
+    int64_t n_periodic;    /* periodic face pairs */
+    int32_t max_faces;     /* most faces of one cell */
+    int32_t n_instances;   /* independent meshes held (1 unless concatenated) */
+    double total_area;     /* sum of cell areas */
+    double min_cfl_length; /* min over cells of A / (Lx + Ly), the length of Eq. (CFL) */
+} fvlbm_mesh_info_t;
+
+typedef struct fvlbm_mesh fvlbm_mesh;
+typedef struct fvlbm_solver fvlbm_solver;
+
+/*
+ * Build a mesh (host only, no GPU needed).
+ *   xy        host, [n_vert][2] vertex coordinates
+ *   cell_ptr  host, [n_cell + 1] offsets into cell_vert (CSR); 3..8 vertices per cell
+ *   cell_vert host, vertex indices of each cell, counter-clockwise
+ *   bedge     host, [n_bedge][2] boundary edges as vertex pairs (either order)
+ *   btag      host, [n_bedge] index into bcs
+ *   bcs       host, [n_bc] boundary conditions
+ * Interior faces are edges shared by two cells; every edge of one cell only
+ * must appear in bedge.  Periodic edges of tag t pair with edges of tag
+ * bcs[t].partner whose midpoint plus bcs[t].shift equals their own.
+ * Computes in FP64 (Sec. 2.2): areas, centroids, face normals and lengths,
+ * least-squares coefficients (Eq. leastsquare), reconstruction vectors
+ * (Eq. lslrflux), the upwind side of every face for every direction, and a
+ * locality-preserving cell order.
+ * Errors: FVLBM_ERR_ARG, _MESH_TOPOLOGY, _DEGENERATE_CELL, _UNTAGGED_BOUNDARY, _OOM.
+ */
+int fvlbm_mesh_create(const double* xy, int64_t n_vert, const int64_t* cell_ptr,
+                      const int32_t* cell_vert, int64_t n_cell, const int32_t* bedge,
+                      const int32_t* btag, int64_t n_bedge, const fvlbm_bc* bcs, int32_t n_bc,
+                      fvlbm_mesh** out);
+
+/*
+ * Concatenate n meshes into one mesh of n independent instances (for a batched
+ * solve: one launch advances all of them).  Cells of instance k follow those
+ * of instance k-1 in the caller's numbering.  The inputs stay valid and owned
+ * by the caller.  Errors: FVLBM_ERR_ARG, _OOM.
+ */
+int fvlbm_mesh_concat(const fvlbm_mesh* const* meshes, int32_t n, fvlbm_mesh** out);
+
+void fvlbm_mesh_destroy(fvlbm_mesh* mesh);
+
+/* Sizes and CFL length of a mesh.  info: host, written. */
+int fvlbm_mesh_info(const fvlbm_mesh* mesh, fvlbm_mesh_info_t* info);
+
+/*
+ * Time step of Eqs. (CFL) and (timetau) for instance `instance`:
+ *   dt = cfl * min_cells(A / (Lx + Ly)) / (sqrt(2) + u_max), capped at 2 tau
+ * (tau for AB2, the paper's observed limit).  Lx, Ly are the cell's extents.
+ * Writes *dt (host).  Errors: FVLBM_ERR_ARG.
+ */
+int fvlbm_suggest_dt(const fvlbm_mesh* mesh, int32_t instance, double tau, double cfl,
+                     double u_max, int32_t scheme, double* dt);
+
+/*
+ * Device bytes fvlbm_init needs when the caller supplies the workspace.
+ * params: host, [n_params] as for fvlbm_init.  bytes: host, written.
+ */
+int fvlbm_workspace_bytes(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t n_params,
+                          size_t* bytes);
+
+/*
+ * Create a solver on params[0].device and set f = f^eq(rho0, u0) (Step 0).
+ *   params     host, one entry per instance of the mesh, or one entry for all
+ *   n_params   1 or the mesh's instance count
+ *   stream     cudaStream_t every kernel and copy of this solver runs on
+ *              (NULL = the legacy default stream)
+ *   workspace  device memory of at least fvlbm_workspace_bytes bytes, aligned to
+ *              256 bytes, owned by the caller and kept alive until
+ *              fvlbm_solver_destroy; NULL = the library allocates its own.
+ * Uploads the packed geometry (blocking on the stream).
+ * Errors: FVLBM_ERR_ARG, _UNSTABLE_DT, _OOM, _CUDA, _UNSUPPORTED.
+ */
+int fvlbm_init(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t n_params,
+               void* stream, void* workspace, size_t workspace_bytes, fvlbm_solver** out);
+
+/*
+ * Advance every instance by n time steps (Steps 1-6, Sec. 2.4 algorithm),
+ * asynchronously on the solver's stream.  A non-finite value raises a device
+ * flag that the next synchronising call reports as FVLBM_ERR_DIVERGED.
+ * Errors: FVLBM_ERR_ARG, _CUDA.
+ */
+int fvlbm_step(fvlbm_solver* s, int64_t n);
+
+/*
+ * Macroscopic fields (Step 6): rho = sum f, rho u = sum f e.
+ *   rho host [n_cell] (may be NULL), u host [n_cell][2] (may be NULL).
+ * Synchronises the stream.  Errors: FVLBM_ERR_ARG, _CUDA, _DIVERGED.
+ */
+int fvlbm_macros(fvlbm_solver* s, double* rho, double* u);
+
+/*
+ * Velocity residual of Sec. 3.2 for each instance,
+ *   e = sqrt(sum_i |u_i - u_i^old|^2) / sqrt(sum_i |u_i^old|^2),
+ * where u^old is the snapshot taken by the previous call (or by fvlbm_init);
+ * then takes a new snapshot.  e = +inf when the snapshot is at rest and the
+ * state is not, 0 when both are at rest.  Sums in FP64, in a fixed order.
+ *   e host [n_instances].  Synchronises.  Errors: FVLBM_ERR_ARG, _CUDA, _DIVERGED.
+ */
+int fvlbm_residual(fvlbm_solver* s, double* e);
+
+/* Total mass sum_i A_i rho_i of each instance, FP64.  mass host [n_instances]. */
+int fvlbm_mass(fvlbm_solver* s, double* mass);
+
+/* Read / write the distribution functions, host [n_cell][9] FP64, caller order.
+ * Writing also restarts AB2 history.  Synchronise. */
+int fvlbm_get_f(fvlbm_solver* s, double* f);
+int fvlbm_set_f(fvlbm_solver* s, const double* f);
+
+/* Wait for the solver's stream; reports FVLBM_ERR_DIVERGED if flagged. */
+int fvlbm_sync(fvlbm_solver* s);
+
+/* Time step in use for instance k (host, written). */
+int fvlbm_get_dt(const fvlbm_solver* s, int32_t instance, double* dt);
+
+void fvlbm_solver_destroy(fvlbm_solver* s);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* fvlbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FVLBM_H */

@@ -1,0 +1,132 @@
+// Internal declarations shared by the host side (mesh, solver) and the CUDA
+// kernels of the library.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include "fvlbm.h"
+
+namespace fvlbm {
+
+// ---------------------------------------------------------------- errors
+// Records a message for fvlbm_last_error() and returns `code`.
+int fail(int code, const char* fmt, ...);
+void clear_error();
+
+// ---------------------------------------------------------------- mesh (host, FP64)
+// Face-slot kinds as the kernels see them.
+enum SlotKind : uint32_t {
+    SK_NONE = 0,      // unused slot (cell has fewer faces)
+    SK_INTERIOR = 1,  // interior or periodic face: neighbour cell across it
+    SK_WALL = 2,
+    SK_INLET = 3,
+    SK_OUTLET = 4,
+    SK_SYMMETRY = 5,
+};
+
+struct Slot {
+    int32_t kind = SK_NONE;  // SlotKind
+    int32_t nb = -1;         // neighbour cell (caller numbering of the instance-local mesh)
+    int32_t nb_slot = -1;    // the same face's slot inside the neighbour
+    int32_t bc = -1;         // boundary tag (boundary slots)
+    int32_t periodic = 0;    // 1 if the face is a periodic pair
+    double nx = 0, ny = 0;   // outward normal times length: (dy, -dx) of the CCW edge
+    double px = 0, py = 0;   // face midpoint
+    double sx = 0, sy = 0;   // periodic: neighbour image = neighbour centroid + (sx, sy)
+    double cgx = 0, cgy = 0; // least-squares coefficient of this slot's stencil point
+    uint32_t outmask = 0;    // bit a-1 set when e_a . n > 0 (a = 1..8): upwind side is this cell
+};
+
+constexpr int MAXP = FVLBM_MAX_POLY;
+
+struct Mesh {
+    int64_t n_cell = 0;
+    int32_t max_faces = 0;
+    int32_t n_inst = 1;
+    std::vector<int64_t> inst_begin;     // [n_inst + 1] cell ranges (same in both numberings)
+    std::vector<int32_t> inst_bc_begin;  // [n_inst + 1] ranges of bcs
+    std::vector<fvlbm_bc> bcs;           // all boundary tags (global numbering)
+    std::vector<double> inst_cfl_len;    // [n_inst] min A/(Lx+Ly)
+    std::vector<int32_t> nf;             // [n_cell] faces per cell
+    std::vector<double> area, cx, cy;    // [n_cell]
+    std::vector<Slot> slots;             // [n_cell * MAXP]; nb is a global caller index
+    std::vector<int64_t> perm;           // internal -> caller
+    std::vector<int64_t> iperm;          // caller -> internal
+    int64_t n_face = 0, n_bface = 0, n_periodic = 0;
+    double total_area = 0;
+};
+
+// ---------------------------------------------------------------- device view
+// Per-instance constants read by the kernels.
+struct InstParam {
+    double tau, inv_tau, dt;
+    float inv_tau_f, dt_f;
+    float scale[FVLBM_Q];      // FP16 storage: stored = g * scale
+    float inv_scale[FVLBM_Q];
+    double rho0, u0x, u0y;
+};
+
+// Per-boundary-tag constants read by the kernels.
+struct BcParam {
+    int32_t kind;      // SlotKind of the tag
+    int32_t external;
+    double uwx, uwy, rho_inf, uix, uiy;
+};
+
+// Device pointers of one solver (all inside one workspace).
+struct DevView {
+    int64_t n_cell;     // cells (internal numbering 0..n_cell-1)
+    int64_t np;         // padded plane length
+    int64_t n_face;     // face-value table length
+    int32_t maxf;       // slots per cell in the packed arrays (4 or 8)
+    int32_t n_inst;
+    // geometry, [maxf][np] planes
+    const int32_t* nbr;
+    const int32_t* fid;
+    const uint32_t* meta;  // kind | outmask << 8 | bc << 16
+    const void* cg;        // T [2][maxf][np]   least-squares coefficients
+    const void* rv;        // T [2][maxf][np]   face midpoint - centroid
+    const void* nv;        // T [2][maxf][np]   (dy, -dx) / A
+    const double* area;    // [np]
+    const int32_t* grp;    // [np] instance of each cell
+    const InstParam* inst; // [n_inst]
+    const BcParam* bc;     // [n_bc]
+    // state
+    void* fa;   // S [9][np]  state
+    void* fb;   // S [9][np]  stage state (multistage schemes)
+    void* rprev;// T [9][np]  AB2 previous RHS
+    void* fv;   // T [8][n_face] face values of directions 1..8
+    double* rho;    // [np]
+    double* ux;     // [np]
+    double* uy;     // [np]
+    double* uold;   // [2][np]
+    double* part;   // [n_chunk][3] block partial sums
+    double* red;    // [n_inst][3]  per-instance sums
+    double* conv;   // [9][np] FP64 staging for get/set of f
+    const int64_t* chunk;   // [n_chunk][3] (begin, end, instance)
+    int64_t n_chunk;
+    int32_t* flag;  // non-finite flag
+};
+
+// Kernel launchers (fvlbm_kernels.cu).  prec = fvlbm_precision.
+int launch_init_eq(const DevView& v, int prec, void* stream);
+int launch_stage(const DevView& v, int prec, void* stream, const void* fin, const void* fbase,
+                 void* fout, double beta, int mode);
+int launch_macros(const DevView& v, int prec, void* stream);
+int launch_reduce(const DevView& v, void* stream, int what);
+int launch_get_f(const DevView& v, int prec, void* stream);
+int launch_set_f(const DevView& v, int prec, void* stream);
+
+// Stage modes of launch_stage.
+enum StageMode { MODE_RK = 0, MODE_AB2_FIRST = 1, MODE_AB2 = 2 };
+// Reductions of launch_reduce.
+enum ReduceWhat { RED_MASS = 0, RED_RESIDUAL = 1 };
+
+}  // namespace fvlbm
+
+struct fvlbm_mesh {
+    fvlbm::Mesh m;
+};

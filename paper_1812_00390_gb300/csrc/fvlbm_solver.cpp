@@ -1,0 +1,555 @@
+// Solver lifecycle and the C ABI entry points that touch the GPU.
+//
+// fvlbm_init packs the FP64 mesh precompute into the device layout of the
+// chosen precision (SoA planes [slot][cell] in the locality order), uploads it
+// into one workspace, and writes Step 0 (f = f^eq).  fvlbm_step enqueues the
+// stages of the time scheme (Sec. 2.3) on the solver's stream.  Everything
+// that reads results back (macros, residual, mass, f) synchronises and maps
+// cells back to the caller's numbering.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include <cuda_runtime.h>
+
+#include "fvlbm_internal.h"
+
+namespace fvlbm {
+double suggest_dt(const Mesh& M, int inst, double tau, double cfl, double umax, int scheme);
+}
+
+using namespace fvlbm;
+
+struct fvlbm_solver {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int prec = FVLBM_FP64;
+    int scheme = FVLBM_EULER;
+    int64_t n_cell = 0;
+    int32_t n_inst = 1;
+    std::vector<int64_t> perm;       // internal -> caller
+    std::vector<int64_t> inst_begin;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    bool own_ws = false;
+    DevView v{};
+    std::vector<InstParam> inst;
+    bool ab2_started = false;
+    std::vector<double> h_conv, h_rho, h_ux, h_uy;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int d) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(FVLBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+constexpr size_t ALIGN = 256;
+constexpr int64_t CHUNK = 4096;
+
+size_t real_size(int prec) { return prec == FVLBM_FP64 ? 8 : 4; }
+size_t store_size(int prec) {
+    return prec == FVLBM_FP64 ? 8 : (prec == FVLBM_FP32_DEV ? 4 : 2);
+}
+
+// Offsets of every array inside the workspace.
+struct Layout {
+    int64_t np, n_face, n_chunk;
+    int maxf;
+    size_t off_nbr, off_fid, off_meta, off_cg, off_rv, off_nv, off_area, off_grp, off_inst, off_bc,
+        off_fa, off_fb, off_rprev, off_fv, off_rho, off_ux, off_uy, off_uold, off_part, off_red, off_conv,
+        off_chunk, off_flag, total;
+};
+
+Layout make_layout(const Mesh& M, int prec, int scheme) {
+    Layout L{};
+    L.np = (M.n_cell + 63) / 64 * 64;
+    L.n_face = M.n_face;
+    L.maxf = M.max_faces <= 4 ? 4 : 8;
+    L.n_chunk = 0;
+    for (int k = 0; k < M.n_inst; k++) L.n_chunk += (M.inst_begin[k + 1] - M.inst_begin[k] + CHUNK - 1) / CHUNK;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = o;
+        o += (bytes + ALIGN - 1) / ALIGN * ALIGN;
+        return r;
+    };
+    const size_t R = real_size(prec), S = store_size(prec);
+    const size_t plane = (size_t)L.np;
+    L.off_nbr = take(4 * plane * L.maxf);
+    L.off_fid = take(4 * plane * L.maxf);
+    L.off_meta = take(4 * plane * L.maxf);
+    L.off_cg = take(R * plane * L.maxf * 2);
+    L.off_rv = take(R * plane * L.maxf * 2);
+    L.off_nv = take(R * plane * L.maxf * 2);
+    L.off_area = take(8 * plane);
+    L.off_grp = take(4 * plane);
+    L.off_inst = take(sizeof(InstParam) * M.n_inst);
+    L.off_bc = take(sizeof(BcParam) * std::max<size_t>(1, M.bcs.size()));
+    L.off_fa = take(S * plane * FVLBM_Q);
+    L.off_fb = (scheme == FVLBM_RK2 || scheme == FVLBM_RK4) ? take(S * plane * FVLBM_Q) : 0;
+    L.off_rprev = scheme == FVLBM_AB2 ? take(R * plane * FVLBM_Q) : 0;
+    L.off_fv = take(R * (size_t)std::max<int64_t>(1, L.n_face) * (FVLBM_Q - 1));
+    L.off_rho = take(8 * plane);
+    L.off_ux = take(8 * plane);
+    L.off_uy = take(8 * plane);
+    L.off_uold = take(16 * plane);
+    L.off_part = take(24 * (size_t)std::max<int64_t>(1, L.n_chunk));
+    L.off_red = take(24 * (size_t)M.n_inst);
+    L.off_conv = take(8 * plane * FVLBM_Q);
+    L.off_chunk = take(24 * (size_t)std::max<int64_t>(1, L.n_chunk));
+    L.off_flag = take(16);
+    L.total = o;
+    return L;
+}
+
+int check_params(const Mesh& M, const fvlbm_params* params, int32_t n_params) {
+    if (!params || !(n_params == 1 || n_params == M.n_inst))
+        return fail(FVLBM_ERR_ARG, "params: need 1 or %d entries, got %d", M.n_inst, n_params);
+    for (int32_t k = 0; k < n_params; k++) {
+        const fvlbm_params& p = params[k];
+        if (!(p.tau > 0) || !(p.dt >= 0) || !(p.cfl >= 0) || !(p.u_max >= 0) || !(p.rho0 > 0))
+            return fail(FVLBM_ERR_ARG, "params[%d]: tau, rho0 must be > 0; dt, cfl, u_max >= 0", k);
+        if (p.scheme < FVLBM_EULER || p.scheme > FVLBM_RK4) return fail(FVLBM_ERR_ARG, "params[%d]: bad scheme", k);
+        if (p.precision < FVLBM_FP64 || p.precision > FVLBM_BF16_DEV)
+            return fail(FVLBM_ERR_ARG, "params[%d]: bad precision", k);
+        if (p.scheme != params[0].scheme || p.precision != params[0].precision || p.device != params[0].device)
+            return fail(FVLBM_ERR_ARG, "params[%d]: scheme, precision and device must match params[0]", k);
+    }
+    if (M.bcs.size() >= 65536) return fail(FVLBM_ERR_ARG, "too many boundary tags (%zu)", M.bcs.size());
+    return FVLBM_OK;
+}
+
+// Largest speed the instance is set up with: |U|_max of Eq. (CFL) when not given.
+double instance_umax(const Mesh& M, int k, const fvlbm_params& p) {
+    if (p.u_max > 0) return p.u_max;
+    double u = std::hypot(p.u0[0], p.u0[1]);
+    for (int32_t b = M.inst_bc_begin[k]; b < M.inst_bc_begin[k + 1]; b++) {
+        const fvlbm_bc& c = M.bcs[b];
+        if (c.kind == FVLBM_BC_WALL) u = std::max(u, std::hypot(c.u_w[0], c.u_w[1]));
+        if (c.kind == FVLBM_BC_INLET || c.kind == FVLBM_BC_OUTLET) u = std::max(u, std::hypot(c.u_inf[0], c.u_inf[1]));
+    }
+    return u;
+}
+
+template <typename T>
+void pack_geometry(const Mesh& M, const Layout& L, std::vector<unsigned char>& host) {
+    const int64_t n = M.n_cell, np = L.np;
+    const int maxf = L.maxf;
+    int32_t* nbr = (int32_t*)(host.data() + L.off_nbr);
+    int32_t* fid = (int32_t*)(host.data() + L.off_fid);
+    uint32_t* meta = (uint32_t*)(host.data() + L.off_meta);
+    T* cg = (T*)(host.data() + L.off_cg);
+    T* rv = (T*)(host.data() + L.off_rv);
+    T* nv = (T*)(host.data() + L.off_nv);
+    double* area = (double*)(host.data() + L.off_area);
+    int32_t* grp = (int32_t*)(host.data() + L.off_grp);
+    for (int64_t x = 0; x < (int64_t)maxf * np; x++) {
+        nbr[x] = -1;
+        fid[x] = -1;
+        meta[x] = SK_NONE;
+    }
+    int64_t next = 0;
+    int32_t g = 0;
+    for (int64_t i = 0; i < n; i++) {
+        const int64_t c = M.perm[i];
+        while (g + 1 < M.n_inst && c >= M.inst_begin[g + 1]) g++;
+        grp[i] = g;
+        area[i] = M.area[c];
+        for (int k = 0; k < M.nf[c]; k++) {
+            const Slot& S = M.slots[(size_t)c * MAXP + k];
+            const int64_t x = (int64_t)k * np + i;
+            meta[x] = (uint32_t)S.kind | (S.outmask << 8) | ((uint32_t)(S.bc < 0 ? 0 : S.bc) << 16);
+            if (S.kind == SK_INTERIOR) {
+                const int64_t j = M.iperm[S.nb];
+                nbr[x] = (int32_t)j;
+                if (fid[x] < 0) {
+                    fid[x] = (int32_t)next;
+                    fid[(int64_t)S.nb_slot * np + j] = (int32_t)next;
+                    next++;
+                }
+            } else {
+                fid[x] = (int32_t)next++;
+            }
+            cg[(0 * maxf + k) * np + i] = (T)S.cgx;
+            cg[(1 * maxf + k) * np + i] = (T)S.cgy;
+            rv[(0 * maxf + k) * np + i] = (T)(S.px - M.cx[c]);
+            rv[(1 * maxf + k) * np + i] = (T)(S.py - M.cy[c]);
+            nv[(0 * maxf + k) * np + i] = (T)(S.nx / M.area[c]);
+            nv[(1 * maxf + k) * np + i] = (T)(S.ny / M.area[c]);
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" int fvlbm_workspace_bytes(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t n_params,
+                                     size_t* bytes) {
+    clear_error();
+    if (!mesh || !bytes) return fail(FVLBM_ERR_ARG, "fvlbm_workspace_bytes: null argument");
+    int rc = check_params(mesh->m, params, n_params);
+    if (rc) return rc;
+    *bytes = make_layout(mesh->m, params[0].precision, params[0].scheme).total;
+    return FVLBM_OK;
+}
+
+static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t n_params, void* stream,
+                     void* workspace, size_t workspace_bytes, fvlbm_solver* s) {
+    const Mesh& M = mesh->m;
+    int rc = check_params(M, params, n_params);
+    if (rc) return rc;
+    const fvlbm_params& p0 = params[0];
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+        return fail(FVLBM_ERR_UNSUPPORTED, "fvlbm_init: no CUDA device");
+    if (p0.device < 0 || p0.device >= ndev) return fail(FVLBM_ERR_ARG, "fvlbm_init: device %d out of range", p0.device);
+    DeviceGuard dg(p0.device);
+    s->device = p0.device;
+    s->stream = (cudaStream_t)stream;
+    s->prec = p0.precision;
+    s->scheme = p0.scheme;
+    s->n_cell = M.n_cell;
+    s->n_inst = M.n_inst;
+    s->perm = M.perm;
+    s->inst_begin = M.inst_begin;
+
+    // per-instance constants and the time step of Eqs. (CFL), (timetau)
+    s->inst.resize(M.n_inst);
+    for (int32_t k = 0; k < M.n_inst; k++) {
+        const fvlbm_params& p = params[n_params == 1 ? 0 : k];
+        InstParam& I = s->inst[k];
+        std::memset(&I, 0, sizeof I);
+        const double umax = instance_umax(M, k, p);
+        double dt = p.dt > 0 ? p.dt : suggest_dt(M, k, p.tau, p.cfl > 0 ? p.cfl : 0.5, umax, p.scheme);
+        const double cap = p.scheme == FVLBM_AB2 ? p.tau : 2.0 * p.tau;
+        if (dt > cap * (1 + 1e-12))
+            return fail(FVLBM_ERR_UNSTABLE_DT, "instance %d: dt = %g exceeds the collision limit %g", k, dt, cap);
+        const double cfl = dt * (std::sqrt(2.0) + umax) / M.inst_cfl_len[k];
+        if (cfl > 1.0 + 1e-12)
+            return fail(FVLBM_ERR_UNSTABLE_DT, "instance %d: dt = %g gives CFL %g > 1", k, dt, cfl);
+        I.tau = p.tau;
+        I.inv_tau = 1.0 / p.tau;
+        I.dt = dt;
+        I.inv_tau_f = (float)I.inv_tau;
+        I.dt_f = (float)dt;
+        I.rho0 = p.rho0;
+        I.u0x = p.u0[0];
+        I.u0y = p.u0[1];
+        for (int a = 0; a < FVLBM_Q; a++) {
+            float sc = 1.0f;
+            if (p.precision == FVLBM_FP16_DEV) {
+                // power-of-two scale that maps the expected |g_a| bound to ~2^12
+                const double w = a == 0 ? 4.0 / 9 : (a < 5 ? 1.0 / 9 : 1.0 / 36);
+                const double e = a == 0 ? 0.0 : (a < 5 ? 1.0 : std::sqrt(2.0));
+                const double U = std::max(umax, 1e-3);
+                const double gmax = w * (0.1 + 1.1 * (3 * e * U + 4.5 * e * e * U * U + 1.5 * U * U));
+                sc = std::ldexp(1.0f, (int)std::floor(std::log2(4096.0 / gmax)));
+            }
+            I.scale[a] = sc;
+            I.inv_scale[a] = 1.0f / sc;
+        }
+    }
+
+    // layout, workspace
+    Layout L = make_layout(M, s->prec, s->scheme);
+    if (workspace) {
+        if (workspace_bytes < L.total)
+            return fail(FVLBM_ERR_OOM, "fvlbm_init: workspace of %zu bytes, %zu needed", workspace_bytes, L.total);
+        if ((uintptr_t)workspace % ALIGN) return fail(FVLBM_ERR_ARG, "fvlbm_init: workspace not 256-byte aligned");
+        s->ws = workspace;
+        s->own_ws = false;
+    } else {
+        cudaError_t e = cudaMalloc(&s->ws, L.total);
+        if (e != cudaSuccess) {
+            s->ws = nullptr;
+            return fail(FVLBM_ERR_OOM, "fvlbm_init: cudaMalloc(%zu): %s", L.total, cudaGetErrorString(e));
+        }
+        s->own_ws = true;
+    }
+    s->ws_bytes = L.total;
+
+    // host image of the read-only part (geometry, params, chunk table)
+    std::vector<unsigned char> host;
+    try {
+        host.assign(L.off_fa, 0);
+        if (s->prec == FVLBM_FP64) pack_geometry<double>(M, L, host);
+        else pack_geometry<float>(M, L, host);
+    } catch (const std::bad_alloc&) {
+        return fail(FVLBM_ERR_OOM, "fvlbm_init: out of host memory");
+    }
+    std::memcpy(host.data() + L.off_inst, s->inst.data(), sizeof(InstParam) * M.n_inst);
+    BcParam* bcp = (BcParam*)(host.data() + L.off_bc);
+    for (size_t b = 0; b < M.bcs.size(); b++) {
+        const fvlbm_bc& c = M.bcs[b];
+        BcParam& q = bcp[b];
+        q.kind = c.kind == FVLBM_BC_WALL ? SK_WALL : c.kind == FVLBM_BC_INLET ? SK_INLET
+               : c.kind == FVLBM_BC_OUTLET ? SK_OUTLET : c.kind == FVLBM_BC_SYMMETRY ? SK_SYMMETRY : SK_NONE;
+        q.external = c.external;
+        q.uwx = c.u_w[0];
+        q.uwy = c.u_w[1];
+        q.rho_inf = c.rho_inf;
+        q.uix = c.u_inf[0];
+        q.uiy = c.u_inf[1];
+    }
+    std::vector<int64_t> chunks;
+    for (int32_t k = 0; k < M.n_inst; k++)
+        for (int64_t b = M.inst_begin[k]; b < M.inst_begin[k + 1]; b += CHUNK)
+            chunks.insert(chunks.end(), {b, std::min(b + CHUNK, M.inst_begin[k + 1]), (int64_t)k});
+
+    unsigned char* base = (unsigned char*)s->ws;
+    CK(cudaMemcpyAsync(base, host.data(), L.off_fa, cudaMemcpyHostToDevice, s->stream), "upload geometry");
+    CK(cudaMemcpyAsync(base + L.off_chunk, chunks.data(), chunks.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                       s->stream), "upload chunk table");
+    // face values start at zero: directions parallel to a face (e.n = 0) are never written
+    CK(cudaMemsetAsync(base + L.off_fv, 0, real_size(s->prec) * (size_t)std::max<int64_t>(1, L.n_face) * (FVLBM_Q - 1),
+                       s->stream), "clear face values");
+    CK(cudaMemsetAsync(base + L.off_flag, 0, 16, s->stream), "clear flag");
+
+    DevView& v = s->v;
+    v.n_cell = M.n_cell;
+    v.np = L.np;
+    v.n_face = L.n_face;
+    v.maxf = L.maxf;
+    v.n_inst = M.n_inst;
+    v.nbr = (const int32_t*)(base + L.off_nbr);
+    v.fid = (const int32_t*)(base + L.off_fid);
+    v.meta = (const uint32_t*)(base + L.off_meta);
+    v.cg = base + L.off_cg;
+    v.rv = base + L.off_rv;
+    v.nv = base + L.off_nv;
+    v.area = (const double*)(base + L.off_area);
+    v.grp = (const int32_t*)(base + L.off_grp);
+    v.inst = (const InstParam*)(base + L.off_inst);
+    v.bc = (const BcParam*)(base + L.off_bc);
+    v.fa = base + L.off_fa;
+    v.fb = L.off_fb ? base + L.off_fb : nullptr;
+    v.rprev = L.off_rprev ? base + L.off_rprev : nullptr;
+    v.fv = base + L.off_fv;
+    v.rho = (double*)(base + L.off_rho);
+    v.ux = (double*)(base + L.off_ux);
+    v.uy = (double*)(base + L.off_uy);
+    v.uold = (double*)(base + L.off_uold);
+    v.part = (double*)(base + L.off_part);
+    v.red = (double*)(base + L.off_red);
+    v.conv = (double*)(base + L.off_conv);
+    v.chunk = (const int64_t*)(base + L.off_chunk);
+    v.n_chunk = (int64_t)chunks.size() / 3;
+    v.flag = (int32_t*)(base + L.off_flag);
+
+    // Step 0 and the first residual snapshot
+    rc = launch_init_eq(v, s->prec, s->stream);
+    if (rc) return rc;
+    rc = launch_macros(v, s->prec, s->stream);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(v.uold, v.ux, 8 * L.np, cudaMemcpyDeviceToDevice, s->stream), "snapshot u");
+    CK(cudaMemcpyAsync(v.uold + L.np, v.uy, 8 * L.np, cudaMemcpyDeviceToDevice, s->stream), "snapshot v");
+    CK(cudaStreamSynchronize(s->stream), "fvlbm_init");
+    try {
+        s->h_conv.resize((size_t)L.np * FVLBM_Q);
+        s->h_rho.resize(L.np);
+        s->h_ux.resize(L.np);
+        s->h_uy.resize(L.np);
+    } catch (const std::bad_alloc&) {
+        return fail(FVLBM_ERR_OOM, "fvlbm_init: out of host memory");
+    }
+    return FVLBM_OK;
+}
+
+extern "C" void fvlbm_solver_destroy(fvlbm_solver* s) {
+    if (!s) return;
+    if (s->own_ws && s->ws) {
+        DeviceGuard dg(s->device);
+        cudaStreamSynchronize(s->stream);
+        cudaFree(s->ws);
+    }
+    delete s;
+}
+
+extern "C" int fvlbm_init(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t n_params, void* stream,
+                          void* workspace, size_t workspace_bytes, fvlbm_solver** out) {
+    clear_error();
+    if (!mesh || !out) return fail(FVLBM_ERR_ARG, "fvlbm_init: null argument");
+    *out = nullptr;
+    fvlbm_solver* s = new (std::nothrow) fvlbm_solver;
+    if (!s) return fail(FVLBM_ERR_OOM, "fvlbm_init: out of host memory");
+    int rc = init_impl(mesh, params, n_params, stream, workspace, workspace_bytes, s);
+    if (rc != FVLBM_OK) {
+        fvlbm_solver_destroy(s);
+        return rc;
+    }
+    *out = s;
+    return FVLBM_OK;
+}
+
+static int enqueue_step(fvlbm_solver* s) {
+    const DevView& v = s->v;
+    switch (s->scheme) {
+        case FVLBM_EULER:
+            return launch_stage(v, s->prec, s->stream, v.fa, v.fa, v.fa, 1.0, MODE_RK);
+        case FVLBM_RK2: {
+            int rc = launch_stage(v, s->prec, s->stream, v.fa, v.fa, v.fb, 0.5, MODE_RK);
+            return rc ? rc : launch_stage(v, s->prec, s->stream, v.fb, v.fa, v.fa, 1.0, MODE_RK);
+        }
+        case FVLBM_RK4: {
+            static const double beta[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
+            for (int k = 0; k < 4; k++) {
+                int rc = launch_stage(v, s->prec, s->stream, k == 0 ? v.fa : v.fb, v.fa, k == 3 ? v.fa : v.fb,
+                                      beta[k], MODE_RK);
+                if (rc) return rc;
+            }
+            return FVLBM_OK;
+        }
+        case FVLBM_AB2: {
+            int rc = launch_stage(v, s->prec, s->stream, v.fa, v.fa, v.fa, 1.0,
+                                  s->ab2_started ? MODE_AB2 : MODE_AB2_FIRST);
+            s->ab2_started = true;
+            return rc;
+        }
+    }
+    return fail(FVLBM_ERR_ARG, "bad scheme");
+}
+
+extern "C" int fvlbm_step(fvlbm_solver* s, int64_t n) {
+    clear_error();
+    if (!s || n < 0) return fail(FVLBM_ERR_ARG, "fvlbm_step: bad arguments");
+    DeviceGuard dg(s->device);
+    for (int64_t k = 0; k < n; k++) {
+        int rc = enqueue_step(s);
+        if (rc) return rc;
+    }
+    return FVLBM_OK;
+}
+
+static int sync_and_check(fvlbm_solver* s) {
+    int32_t flag = 0;
+    CK(cudaMemcpyAsync(&flag, s->v.flag, sizeof flag, cudaMemcpyDeviceToHost, s->stream), "read flag");
+    CK(cudaStreamSynchronize(s->stream), "synchronise");
+    if (flag) return fail(FVLBM_ERR_DIVERGED, "a non-finite value appeared in the state");
+    return FVLBM_OK;
+}
+
+extern "C" int fvlbm_sync(fvlbm_solver* s) {
+    clear_error();
+    if (!s) return fail(FVLBM_ERR_ARG, "fvlbm_sync: null solver");
+    DeviceGuard dg(s->device);
+    return sync_and_check(s);
+}
+
+extern "C" int fvlbm_macros(fvlbm_solver* s, double* rho, double* u) {
+    clear_error();
+    if (!s) return fail(FVLBM_ERR_ARG, "fvlbm_macros: null solver");
+    DeviceGuard dg(s->device);
+    int rc = launch_macros(s->v, s->prec, s->stream);
+    if (rc) return rc;
+    const size_t bytes = 8 * (size_t)s->n_cell;
+    CK(cudaMemcpyAsync(s->h_rho.data(), s->v.rho, bytes, cudaMemcpyDeviceToHost, s->stream), "read rho");
+    CK(cudaMemcpyAsync(s->h_ux.data(), s->v.ux, bytes, cudaMemcpyDeviceToHost, s->stream), "read ux");
+    CK(cudaMemcpyAsync(s->h_uy.data(), s->v.uy, bytes, cudaMemcpyDeviceToHost, s->stream), "read uy");
+    rc = sync_and_check(s);
+    if (rc) return rc;
+    for (int64_t i = 0; i < s->n_cell; i++) {
+        const int64_t c = s->perm[i];
+        if (rho) rho[c] = s->h_rho[i];
+        if (u) {
+            u[2 * c] = s->h_ux[i];
+            u[2 * c + 1] = s->h_uy[i];
+        }
+    }
+    return FVLBM_OK;
+}
+
+static int reduce(fvlbm_solver* s, int what, std::vector<double>& out) {
+    int rc = launch_macros(s->v, s->prec, s->stream);
+    if (rc) return rc;
+    rc = launch_reduce(s->v, s->stream, what);
+    if (rc) return rc;
+    out.assign(3 * (size_t)s->n_inst, 0.0);
+    CK(cudaMemcpyAsync(out.data(), s->v.red, out.size() * 8, cudaMemcpyDeviceToHost, s->stream), "read sums");
+    return sync_and_check(s);
+}
+
+extern "C" int fvlbm_residual(fvlbm_solver* s, double* e) {
+    clear_error();
+    if (!s || !e) return fail(FVLBM_ERR_ARG, "fvlbm_residual: null argument");
+    DeviceGuard dg(s->device);
+    std::vector<double> r;
+    int rc = reduce(s, RED_RESIDUAL, r);
+    if (rc) return rc;
+    for (int32_t k = 0; k < s->n_inst; k++) {
+        const double num = r[3 * k], den = r[3 * k + 1];
+        e[k] = den == 0 ? (num == 0 ? 0.0 : INFINITY) : std::sqrt(num) / std::sqrt(den);
+    }
+    return FVLBM_OK;
+}
+
+extern "C" int fvlbm_mass(fvlbm_solver* s, double* mass) {
+    clear_error();
+    if (!s || !mass) return fail(FVLBM_ERR_ARG, "fvlbm_mass: null argument");
+    DeviceGuard dg(s->device);
+    std::vector<double> r;
+    int rc = reduce(s, RED_MASS, r);
+    if (rc) return rc;
+    for (int32_t k = 0; k < s->n_inst; k++) mass[k] = r[3 * k];
+    return FVLBM_OK;
+}
+
+extern "C" int fvlbm_get_f(fvlbm_solver* s, double* f) {
+    clear_error();
+    if (!s || !f) return fail(FVLBM_ERR_ARG, "fvlbm_get_f: null argument");
+    DeviceGuard dg(s->device);
+    int rc = launch_get_f(s->v, s->prec, s->stream);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(s->h_conv.data(), s->v.conv, 8 * (size_t)s->v.np * FVLBM_Q, cudaMemcpyDeviceToHost, s->stream),
+       "read f");
+    rc = sync_and_check(s);
+    if (rc) return rc;
+    for (int64_t i = 0; i < s->n_cell; i++) {
+        const int64_t c = s->perm[i];
+        for (int a = 0; a < FVLBM_Q; a++) f[c * FVLBM_Q + a] = s->h_conv[(size_t)a * s->v.np + i];
+    }
+    return FVLBM_OK;
+}
+
+extern "C" int fvlbm_set_f(fvlbm_solver* s, const double* f) {
+    clear_error();
+    if (!s || !f) return fail(FVLBM_ERR_ARG, "fvlbm_set_f: null argument");
+    DeviceGuard dg(s->device);
+    CK(cudaStreamSynchronize(s->stream), "synchronise");
+    for (int64_t i = 0; i < s->n_cell; i++) {
+        const int64_t c = s->perm[i];
+        for (int a = 0; a < FVLBM_Q; a++) s->h_conv[(size_t)a * s->v.np + i] = f[c * FVLBM_Q + a];
+    }
+    CK(cudaMemcpyAsync(s->v.conv, s->h_conv.data(), 8 * (size_t)s->v.np * FVLBM_Q, cudaMemcpyHostToDevice, s->stream),
+       "write f");
+    int rc = launch_set_f(s->v, s->prec, s->stream);
+    if (rc) return rc;
+    s->ab2_started = false;
+    CK(cudaStreamSynchronize(s->stream), "synchronise");
+    return FVLBM_OK;
+}
+
+extern "C" int fvlbm_get_dt(const fvlbm_solver* s, int32_t instance, double* dt) {
+    clear_error();
+    if (!s || !dt || instance < 0 || instance >= s->n_inst) return fail(FVLBM_ERR_ARG, "fvlbm_get_dt: bad arguments");
+    *dt = s->inst[instance].dt;
+    return FVLBM_OK;
+}

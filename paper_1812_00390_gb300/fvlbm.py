@@ -1,0 +1,268 @@
+"""Python binding of libfvlbm (ctypes over the C ABI in include/fvlbm.h).
+
+Argument marshalling only: every step of the solver runs in the library's CUDA
+kernels.  PyTorch supplies the device workspace and the stream.  There is no
+fallback: if the shared library is missing or cannot be loaded, importing this
+module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Iterable, List, Optional, Sequence, Union
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfvlbm.so")
+
+EULER, RK2, AB2, RK4 = 0, 1, 2, 3
+FP64, FP32_DEV, FP16_DEV, BF16_DEV = 0, 1, 2, 3
+SCHEMES = {"euler": EULER, "rk2": RK2, "ab2": AB2, "rk4": RK4}
+PRECISIONS = {"fp64": FP64, "fp32": FP32_DEV, "fp16": FP16_DEV, "bf16": BF16_DEV}
+
+ERRORS = {
+    -1: "ARG", -2: "MESH_TOPOLOGY", -3: "DEGENERATE_CELL", -4: "UNTAGGED_BOUNDARY",
+    -5: "UNSTABLE_DT", -6: "OOM", -7: "CUDA", -8: "DIVERGED", -9: "TIMEOUT", -10: "UNSUPPORTED",
+}
+
+
+class FvlbmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+        super().__init__(f"FVLBM_ERR_{self.name}: {msg}")
+
+
+class BcT(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("external", C.c_int32), ("u_w", C.c_double * 2),
+                ("rho_inf", C.c_double), ("u_inf", C.c_double * 2), ("partner", C.c_int32),
+                ("reserved", C.c_int32), ("shift", C.c_double * 2)]
+
+
+class ParamsT(C.Structure):
+    _fields_ = [("tau", C.c_double), ("dt", C.c_double), ("cfl", C.c_double), ("u_max", C.c_double),
+                ("scheme", C.c_int32), ("precision", C.c_int32), ("rho0", C.c_double),
+                ("u0", C.c_double * 2), ("device", C.c_int32), ("reserved", C.c_int32)]
+
+
+class MeshInfoT(C.Structure):
+    _fields_ = [("n_cell", C.c_int64), ("n_face", C.c_int64), ("n_bface", C.c_int64),
+                ("n_periodic", C.c_int64), ("max_faces", C.c_int32), ("n_instances", C.c_int32),
+                ("total_area", C.c_double), ("min_cfl_length", C.c_double)]
+
+
+#: every symbol include/fvlbm.h declares
+EXPORTS = ["fvlbm_mesh_create", "fvlbm_mesh_concat", "fvlbm_mesh_destroy", "fvlbm_mesh_info",
+           "fvlbm_suggest_dt", "fvlbm_workspace_bytes", "fvlbm_init", "fvlbm_step", "fvlbm_macros",
+           "fvlbm_residual", "fvlbm_mass", "fvlbm_get_f", "fvlbm_set_f", "fvlbm_sync",
+           "fvlbm_get_dt", "fvlbm_solver_destroy", "fvlbm_last_error"]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run __graft_entry__.build() "
+                          "(the solver has no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    PP = C.POINTER(C.c_void_p)
+    dp = C.POINTER(C.c_double)
+    i32p = C.POINTER(C.c_int32)
+    i64p = C.POINTER(C.c_int64)
+    sig = {
+        "fvlbm_mesh_create": [dp, C.c_int64, i64p, i32p, C.c_int64, i32p, i32p, C.c_int64,
+                              C.POINTER(BcT), C.c_int32, PP],
+        "fvlbm_mesh_concat": [PP, C.c_int32, PP],
+        "fvlbm_mesh_destroy": [P],
+        "fvlbm_mesh_info": [P, C.POINTER(MeshInfoT)],
+        "fvlbm_suggest_dt": [P, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_int32, dp],
+        "fvlbm_workspace_bytes": [P, C.POINTER(ParamsT), C.c_int32, C.POINTER(C.c_size_t)],
+        "fvlbm_init": [P, C.POINTER(ParamsT), C.c_int32, P, P, C.c_size_t, PP],
+        "fvlbm_step": [P, C.c_int64],
+        "fvlbm_macros": [P, dp, dp],
+        "fvlbm_residual": [P, dp],
+        "fvlbm_mass": [P, dp],
+        "fvlbm_get_f": [P, dp],
+        "fvlbm_set_f": [P, dp],
+        "fvlbm_sync": [P],
+        "fvlbm_get_dt": [P, C.c_int32, dp],
+        "fvlbm_solver_destroy": [P],
+        "fvlbm_last_error": [],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    lib.fvlbm_mesh_destroy.restype = None
+    lib.fvlbm_solver_destroy.restype = None
+    lib.fvlbm_last_error.restype = C.c_char_p
+    return lib
+
+
+lib = _load()
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise FvlbmError(rc, (lib.fvlbm_last_error() or b"").decode())
+
+
+def _d(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Mesh:
+    """A mesh handle built from a meshgen.Mesh (or any object with the same arrays)."""
+
+    def __init__(self, m=None, _handle=None, _n_cell=None):
+        if _handle is not None:
+            self._h = _handle
+            self.n_cell = _n_cell
+            return
+        xy = np.ascontiguousarray(m.xy, np.float64)
+        cp = np.ascontiguousarray(m.cell_ptr, np.int64)
+        cv = np.ascontiguousarray(m.cell_vert, np.int32)
+        be = np.ascontiguousarray(m.bedge, np.int32)
+        bt = np.ascontiguousarray(m.btag, np.int32)
+        bcs = (BcT * max(1, len(m.bcs)))()
+        for i, b in enumerate(m.bcs):
+            bcs[i].kind = b.kind
+            bcs[i].external = b.external
+            bcs[i].u_w[:] = list(b.u_w)
+            bcs[i].rho_inf = b.rho_inf
+            bcs[i].u_inf[:] = list(b.u_inf)
+            bcs[i].partner = b.partner
+            bcs[i].shift[:] = list(b.shift)
+        h = C.c_void_p()
+        _check(lib.fvlbm_mesh_create(_d(xy), xy.shape[0], cp.ctypes.data_as(C.POINTER(C.c_int64)),
+                                     cv.ctypes.data_as(C.POINTER(C.c_int32)), cp.shape[0] - 1,
+                                     be.ctypes.data_as(C.POINTER(C.c_int32)),
+                                     bt.ctypes.data_as(C.POINTER(C.c_int32)), be.shape[0], bcs,
+                                     len(m.bcs), C.byref(h)))
+        self._h = h
+        self.n_cell = int(cp.shape[0] - 1)
+
+    @classmethod
+    def concat(cls, meshes: Sequence["Mesh"]) -> "Mesh":
+        arr = (C.c_void_p * len(meshes))(*[m._h.value for m in meshes])
+        h = C.c_void_p()
+        _check(lib.fvlbm_mesh_concat(arr, len(meshes), C.byref(h)))
+        return cls(_handle=h, _n_cell=sum(m.n_cell for m in meshes))
+
+    def info(self) -> dict:
+        i = MeshInfoT()
+        _check(lib.fvlbm_mesh_info(self._h, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in MeshInfoT._fields_}
+
+    def suggest_dt(self, tau: float, cfl: float = 0.5, u_max: float = 0.1, scheme="euler",
+                   instance: int = 0) -> float:
+        dt = C.c_double()
+        _check(lib.fvlbm_suggest_dt(self._h, instance, tau, cfl, u_max, _scheme(scheme), C.byref(dt)))
+        return dt.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib.fvlbm_mesh_destroy(h)
+            self._h = None
+
+
+def _scheme(s) -> int:
+    return SCHEMES[s] if isinstance(s, str) else int(s)
+
+
+def _prec(p) -> int:
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+def make_params(tau: float, dt: float = 0.0, scheme="euler", precision="fp64", rho0: float = 1.0,
+                u0=(0.0, 0.0), cfl: float = 0.0, u_max: float = 0.0, device: int = 0) -> ParamsT:
+    p = ParamsT()
+    p.tau, p.dt, p.cfl, p.u_max = tau, dt, cfl, u_max
+    p.scheme, p.precision = _scheme(scheme), _prec(precision)
+    p.rho0 = rho0
+    p.u0[:] = list(u0)
+    p.device = device
+    return p
+
+
+class Solver:
+    """Solver of one mesh (possibly a concatenation of instances) on one GPU.
+
+    params: one ParamsT (all instances) or one per instance.  The device
+    workspace is a torch uint8 tensor on the solver's device, kept alive by this
+    object; the stream is torch's current stream on that device unless given.
+    """
+
+    def __init__(self, mesh: Mesh, params: Union[ParamsT, Sequence[ParamsT]], stream=None,
+                 use_torch_workspace: bool = True):
+        import torch
+        plist = [params] if isinstance(params, ParamsT) else list(params)
+        arr = (ParamsT * len(plist))(*plist)
+        dev = plist[0].device
+        self.device = dev
+        self.mesh = mesh
+        self.n_cell = mesh.n_cell
+        self.n_inst = mesh.info()["n_instances"]
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        self.stream = stream
+        sh = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+        nbytes = C.c_size_t()
+        _check(lib.fvlbm_workspace_bytes(mesh._h, arr, len(plist), C.byref(nbytes)))
+        self.workspace_bytes = nbytes.value
+        if use_torch_workspace:
+            self._ws = torch.empty(nbytes.value, dtype=torch.uint8, device=f"cuda:{dev}")
+            ws_ptr = self._ws.data_ptr()
+        else:
+            self._ws = None
+            ws_ptr = None
+        h = C.c_void_p()
+        _check(lib.fvlbm_init(mesh._h, arr, len(plist), C.c_void_p(sh), C.c_void_p(ws_ptr),
+                              nbytes.value, C.byref(h)))
+        self._h = h
+
+    def step(self, n: int = 1):
+        _check(lib.fvlbm_step(self._h, int(n)))
+
+    def sync(self):
+        _check(lib.fvlbm_sync(self._h))
+
+    def macros(self):
+        rho = np.zeros(self.n_cell)
+        u = np.zeros((self.n_cell, 2))
+        _check(lib.fvlbm_macros(self._h, _d(rho), _d(u)))
+        return rho, u
+
+    def residual(self) -> np.ndarray:
+        e = np.zeros(self.n_inst)
+        _check(lib.fvlbm_residual(self._h, _d(e)))
+        return e
+
+    def mass(self) -> np.ndarray:
+        m = np.zeros(self.n_inst)
+        _check(lib.fvlbm_mass(self._h, _d(m)))
+        return m
+
+    def get_f(self) -> np.ndarray:
+        f = np.zeros((self.n_cell, 9))
+        _check(lib.fvlbm_get_f(self._h, _d(f)))
+        return f
+
+    def set_f(self, f):
+        f = np.ascontiguousarray(f, np.float64).reshape(self.n_cell, 9)
+        _check(lib.fvlbm_set_f(self._h, _d(f)))
+
+    def dt(self, instance: int = 0) -> float:
+        d = C.c_double()
+        _check(lib.fvlbm_get_dt(self._h, instance, C.byref(d)))
+        return d.value
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib.fvlbm_solver_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()

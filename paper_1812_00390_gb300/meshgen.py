@@ -398,3 +398,30 @@ def batch_specs(n: int = 256, seed: int = 2018, re_lo: float = 10.0, re_hi: floa
         re = float(np.exp(rng.uniform(np.log(re_lo), np.log(re_hi))))
         out.append({"kind": kinds[k % 3], "re": re, "seed": int(rng.integers(1 << 30))})
     return out
+
+
+def bricks(nx: int = 8, ny: int = 6, U: float = 0.1, lx: float = 1.0, ly: float = 1.0) -> Mesh:
+    """Running-bond brick mesh of a walled box: most cells are hexagons (two grid
+    squares merged, with a straight-through vertex in the middle of each long
+    side), row ends are single squares.  Exercises cells with up to 6 faces.
+    Lid (top) moves at (U, 0)."""
+    if nx % 2:
+        raise ValueError("nx must be even")
+    hx, hy = lx / nx, ly / ny
+    xy = _grid_vertices(np.arange(nx + 1) * hx, np.arange(ny + 1) * hy)
+    vid = lambda i, j: j * (nx + 1) + i
+    cells = []
+    for j in range(ny):
+        i = 0
+        if j % 2 == 1:
+            cells.append((vid(0, j), vid(1, j), vid(1, j + 1), vid(0, j + 1)))
+            i = 1
+        while i + 2 <= nx:
+            cells.append((vid(i, j), vid(i + 1, j), vid(i + 2, j), vid(i + 2, j + 1),
+                          vid(i + 1, j + 1), vid(i, j + 1)))
+            i += 2
+        if i < nx:
+            cells.append((vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)))
+    be, bt = _rect_boundary(nx, ny, vid, (0, 0, 1, 0))
+    bcs = [BC(BC_WALL), BC(BC_WALL, u_w=(U, 0.0))]
+    return _pack(xy, cells, be, bt, bcs, f"bricks{nx}x{ny}")

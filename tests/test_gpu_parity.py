@@ -1,0 +1,235 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+FP64 mode: every distribution function agrees with the oracle to 1e-12
+relative (to the largest |f|), on every mesh type, boundary kind and time
+scheme.  Deviation modes: the error against the FP64 oracle stays within the
+bound stated for each storage type.
+"""
+import numpy as np
+import pytest
+
+from paper_1812_00390_gb300 import meshgen as mg
+from paper_1812_00390_gb300.meshgen import BC, BC_INLET, BC_OUTLET, BC_SYMMETRY, BC_WALL
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def fv():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1812_00390_gb300 import fvlbm
+    return fvlbm
+
+
+def f_random(orc, m, seed, noise=0.05):
+    rho, u, dev = mg.random_state(m.n_cell, seed=seed)
+    return np.array([orc.feq(r, *v) for r, v in zip(rho, u)]) + noise * dev
+
+
+def poiseuille_channel():
+    m = mg.channel(nx=20, ny=6, lx=2.0, ly=0.6, u_inf=(0.05, 0.0), top_bottom="inlet", external=0)
+    ym = m.xy[m.bedge, 1].mean(1)
+    bt = m.btag.copy()
+    bt[(np.abs(ym) < 1e-12) | (np.abs(ym - 0.6) < 1e-12)] = 2
+    m.btag = bt
+    m.bcs = [BC(BC_INLET, external=0, u_inf=(0.05, 0.0)), BC(BC_OUTLET, external=0, rho_inf=1.0), BC(BC_WALL)]
+    return m
+
+
+MESHES = {
+    "couette": lambda: mg.couette(),
+    "periodic_tri": lambda: mg.periodic_tri(12, 10, lx=12.0, ly=10.0),
+    "periodic_quad": lambda: mg.periodic_quad(10, 8, lx=10.0, ly=8.0),
+    "cavity_quad": lambda: mg.cavity(24, 8.0),
+    "cavity_tri": lambda: mg.cavity(16, 4.0, triangles=True),
+    "bricks": lambda: mg.bricks(10, 8),
+    "cylinder": lambda: mg.cylinder_hybrid(n_rad=8, n_circ=32, first=0.02, growth=1.15, r_far=8.0,
+                                           n_tri_rings=8, seed=4),
+    "far_field": lambda: mg.channel(nx=16, ny=8, u_inf=(0.05, 0.01)),
+    "internal_io": poiseuille_channel,
+    "symmetry": lambda: mg.channel(nx=14, ny=6, top_bottom="symmetry"),
+    "two_tri_wall": lambda: mg.two_triangles(),
+    "two_tri_periodic": lambda: mg.two_triangles(periodic=True),
+}
+
+
+def run_both(fv, orc, m, scheme, prec, tau, dt, nsteps, f0):
+    s = fv.Solver(fv.Mesh(m), fv.make_params(tau, dt=dt, scheme=scheme, precision=prec))
+    s.set_f(f0)
+    s.step(nsteps)
+    got = s.get_f()
+    o = orc.Oracle(m)
+    o.set_f(f0)
+    o.run(scheme, tau, dt, nsteps)
+    return got, o.get_f(), s, o
+
+
+def rel_err(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.mark.parametrize("name", list(MESHES))
+@pytest.mark.parametrize("scheme", ["euler", "rk2", "rk4", "ab2"])
+def test_fp64_parity_every_mesh_and_scheme(fv, orc, name, scheme):
+    m = MESHES[name]()
+    tau = 0.2
+    o = orc.Oracle(m)
+    dt = o.cfl_dt(0.5, 0.1, tau, scheme)
+    f0 = f_random(orc, m, seed=sum(map(ord, name)))
+    got, ref, s, _ = run_both(fv, orc, m, scheme, "fp64", tau, dt, 25, f0)
+    assert rel_err(got, ref) < FP64_TOL
+    s.close()
+
+
+def test_couette_config_fp64(fv, orc):
+    """32x8 jittered Couette channel, Re = 10, explicit Euler, 2000 steps from rest
+    (Step 0 done on each side): FP64 parity, then the closed-form profile."""
+    m = mg.couette()
+    tau = 3 * 0.1 * 8 / 10
+    mesh = fv.Mesh(m)
+    s = fv.Solver(mesh, fv.make_params(tau, scheme="euler", precision="fp64"))
+    o = orc.Oracle(m)
+    dt = o.cfl_dt(0.5, 0.1, tau, "euler")
+    assert s.dt() == pytest.approx(dt, rel=1e-15)
+    s.step(2000)
+    o.set_equilibrium(1.0, (0.0, 0.0))
+    o.run("euler", tau, dt, 2000)
+    assert rel_err(s.get_f(), o.get_f()) < FP64_TOL
+    rho_g, u_g = s.macros()
+    rho_o, u_o = o.macros()
+    assert np.abs(u_g - u_o).max() < 1e-12 * 0.1
+    assert np.abs(rho_g - rho_o).max() < 1e-12
+    _, c, _ = o.geometry()
+    y, t, H, nu = c[:, 1], 2000 * dt, 8.0, tau / 3
+    ex = 0.1 * y / H
+    for k in range(1, 400):
+        ex += 0.2 * (-1) ** k / (k * np.pi) * np.sin(k * np.pi * y / H) * np.exp(-(k * np.pi) ** 2 * nu * t / H ** 2)
+    assert np.abs(u_g[:, 0] - ex).max() < 6e-4
+
+
+def test_macros_mass_residual_parity(fv, orc):
+    m = mg.cavity(20, 6.0)
+    tau = 0.05
+    o = orc.Oracle(m)
+    dt = o.cfl_dt(0.5, 0.1, tau, "rk2")
+    f0 = f_random(orc, m, seed=5)
+    s = fv.Solver(fv.Mesh(m), fv.make_params(tau, dt=dt, scheme="rk2", precision="fp64"))
+    s.set_f(f0)
+    o.set_f(f0)
+    s.residual()                       # snapshot at f0
+    _, u_old = o.macros()
+    s.step(40)
+    o.run("rk2", tau, dt, 40)
+    e_gpu = s.residual()[0]
+    e_orc = o.residual(u_old)
+    assert abs(e_gpu - e_orc) <= 1e-12 * e_orc
+    a, _, _ = o.geometry()
+    assert abs(s.mass()[0] - o.mass()) <= 1e-13 * o.mass()
+    rg, ug = s.macros()
+    ro, uo = o.macros()
+    assert np.abs(rg - ro).max() < 1e-12 and np.abs(ug - uo).max() < 1e-13
+    # a second residual right away is zero; from rest it is +inf
+    assert s.residual()[0] == 0.0
+    s2 = fv.Solver(fv.Mesh(m), fv.make_params(tau, dt=dt, scheme="rk2"))
+    s2.step(3)
+    assert s2.residual()[0] == np.inf
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_mass_conservation(fv, prec):
+    for m in (mg.couette(), mg.cavity(32, 10.0)):
+        s = fv.Solver(fv.Mesh(m), fv.make_params(0.1, scheme="rk2", precision=prec))
+        m0 = s.mass()[0]
+        n = 2000
+        s.step(n)
+        drift = abs(s.mass()[0] - m0) / m0
+        assert drift < (n * 1e-15 if prec == "fp64" else 1e-6), drift
+
+
+def test_batch_equals_solo(fv, orc):
+    """Instances concatenated into one solver give bitwise the same state as each
+    solved alone (per-instance tau and dt)."""
+    meshes = [mg.couette(16, 6), mg.cavity(12, 5.0), mg.cylinder_hybrid(n_rad=6, n_circ=24, first=0.05,
+                                                                          growth=1.2, r_far=6.0, n_tri_rings=5)]
+    taus = [0.24, 0.05, 0.1]
+    for prec in ("fp64", "fp32"):
+        handles = [fv.Mesh(m) for m in meshes]
+        solo = []
+        for h, t in zip(handles, taus):
+            s = fv.Solver(h, fv.make_params(t, scheme="rk2", precision=prec))
+            s.step(30)
+            solo.append(s.get_f())
+        cat = fv.Mesh.concat(handles)
+        sb = fv.Solver(cat, [fv.make_params(t, scheme="rk2", precision=prec) for t in taus])
+        for k, h in enumerate(handles):
+            assert sb.dt(k) == pytest.approx(fv.Solver(h, fv.make_params(taus[k], scheme="rk2",
+                                                                           precision=prec)).dt())
+        sb.step(30)
+        fb = sb.get_f()
+        off = 0
+        for k, m in enumerate(meshes):
+            assert np.array_equal(fb[off:off + m.n_cell], solo[k]), (prec, k)
+            off += m.n_cell
+
+
+def test_cavity_fp32_velocity_error(fv, orc):
+    """Lid-driven cavity 128^2 (tanh-stretched, 1:20), Re = 400, RK2, 10^4 steps:
+    FP32 deviation mode against the FP64 oracle, relative velocity error <= 1e-5."""
+    m = mg.cavity(128, 20.0, U=0.1)
+    tau = 3 * 0.1 / 400
+    o = orc.Oracle(m)
+    dt = o.cfl_dt(0.5, 0.1, tau, "rk2")
+    s = fv.Solver(fv.Mesh(m), fv.make_params(tau, dt=dt, scheme="rk2", precision="fp32"))
+    n = 10000
+    s.step(n)
+    o.set_equilibrium(1.0, (0.0, 0.0))
+    o.run("rk2", tau, dt, n)
+    _, ug = s.macros()
+    _, uo = o.macros()
+    err = np.abs(ug - uo).max() / np.abs(uo).max()
+    assert err < 1e-5, err
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp16", 2e-3), ("bf16", 2e-2)])
+def test_deviation_modes_error_bound(fv, orc, prec, tol):
+    """Stored-precision error after 500 RK2 steps of a cylinder hybrid mesh (far
+    field, wall), relative to the largest velocity."""
+    m = mg.cylinder_hybrid(n_rad=10, n_circ=40, first=0.01, growth=1.15, r_far=10.0, n_tri_rings=10)
+    tau = 3 * 0.05 * 1.0 / 40
+    o = orc.Oracle(m)
+    dt = o.cfl_dt(0.5, 0.05, tau, "rk2")
+    s = fv.Solver(fv.Mesh(m), fv.make_params(tau, dt=dt, scheme="rk2", precision=prec, u0=(0.05, 0.0)))
+    s.step(500)
+    o.set_equilibrium(1.0, (0.05, 0.0))
+    o.run("rk2", tau, dt, 500)
+    _, ug = s.macros()
+    _, uo = o.macros()
+    err = np.abs(ug - uo).max() / np.abs(uo).max()
+    assert err < tol, err
+
+
+def test_edge_cases(fv, orc):
+    m = mg.two_triangles()
+    s = fv.Solver(fv.Mesh(m), fv.make_params(0.2, scheme="rk2"))
+    f = s.get_f()
+    s.step(0)
+    assert np.array_equal(s.get_f(), f)
+    with pytest.raises(fv.FvlbmError) as e:
+        fv.Solver(fv.Mesh(m), fv.make_params(0.2, dt=0.5, scheme="euler"))
+    assert e.value.name == "UNSTABLE_DT"
+    with pytest.raises(fv.FvlbmError) as e:
+        fv.Solver(fv.Mesh(m), fv.make_params(0.2, dt=0.3, scheme="ab2"))
+    assert e.value.name == "UNSTABLE_DT"
+    # a non-finite state is reported at the next synchronising call
+    bad = f.copy()
+    bad[1, 3] = np.nan
+    s.set_f(bad)
+    s.step(2)
+    with pytest.raises(fv.FvlbmError) as e:
+        s.sync()
+    assert e.value.name == "DIVERGED"
