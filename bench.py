@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""Throughput of the FVLBM D2Q9 step on one or more GB300 GPUs.
+
+Workload (default): a batched solve of 256 heterogeneous instances advanced by
+one launch sequence per stage -- jittered Couette channels (64x16, 2048
+triangles), tanh-stretched lid-driven cavities (128^2 quads, 1:20) and
+cylinder hybrids (100x200 O-grid quads + 100 rings of triangles, 60,000 cells)
+in thirds, Reynolds number log-uniform in [10, 1000] (seed 2018), RK2, FP32
+arithmetic on the deviation g = f - w.  ~6.7 M cells; the f state alone is
+~240 MB, larger than the 129 MB L2, so no L2 flush is needed between steps.
+
+One JSON line on rank 0: MCUPS (million cell updates per second; an RK2 step
+counts once), the same workload in FP64 for the mixed/FP64 ratio and its
+error, the roofline of the stage kernels, the CPU oracle baseline, an
+end-to-end number through the C ABI with host buffers, and the SM clocks seen.
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "D2Q9 MCUPS mixed vs FP64 at fixed error, %HBM peak; p50/p99 solve latency"
+HBM_FALLBACK_GBS = 6800.0
+
+
+# ----------------------------------------------------------------------------- workload
+def batch_instances(n_inst: int, seed: int = 2018, small: bool = False):
+    """(meshgen meshes by variant, list of (variant key, tau, u0)) for the batch."""
+    from paper_1812_00390_gb300 import meshgen as mg
+    specs = mg.batch_specs(n_inst, seed=seed)
+    variants = {}
+    out = []
+    for k, sp in enumerate(specs):
+        kind, re_ = sp["kind"], sp["re"]
+        if kind == "couette":
+            key = ("couette", k % 4)
+            if key not in variants:
+                variants[key] = mg.couette(nx=16 if small else 64, ny=4 if small else 16, U=0.1,
+                                           seed=1812 + key[1])
+            H = 4.0 if small else 16.0
+            tau = 3.0 * 0.1 * H / re_
+            u0 = (0.0, 0.0)
+        elif kind == "cavity":
+            key = ("cavity", 0)
+            if key not in variants:
+                variants[key] = mg.cavity(32 if small else 128, 20.0, U=0.1)
+            tau = 3.0 * 0.1 * 1.0 / re_
+            u0 = (0.0, 0.0)
+        else:
+            key = ("cylinder", k % 2)
+            if key not in variants:
+                variants[key] = (mg.cylinder_hybrid(n_rad=25, n_circ=50, n_tri_rings=25, seed=100 + key[1])
+                                 if small else mg.cylinder_hybrid(seed=100 + key[1]))
+            tau = 3.0 * 0.05 * 1.0 / re_
+            u0 = (0.05, 0.0)
+        out.append((key, tau, u0))
+    return variants, out
+
+
+def build_solver(fv, variants, inst, precision, scheme="rk2", handles=None):
+    handles = handles or {k: fv.Mesh(m) for k, m in variants.items()}
+    mesh = fv.Mesh.concat([handles[k] for k, _, _ in inst])
+    params = [fv.make_params(tau, scheme=scheme, precision=precision, u0=u0) for _, tau, u0 in inst]
+    return fv.Solver(mesh, params), handles
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self._t.join(timeout=5)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- roofline inputs
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except (ValueError, OSError):
+            pass
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+def kernel_source_sha() -> str:
+    src = os.path.join(ROOT, "paper_1812_00390_gb300", "csrc", "fvlbm_kernels.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def ncu_traffic(workload: str):
+    """DRAM bytes per cell and stage from the committed ncu summary of this
+    workload, or None when it is missing or was taken on other kernel source."""
+    p = os.path.join(ROOT, "profiles", f"stage_kernels_{workload}.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", txt)
+    t = re.search(r"dram_bytes_per_cell_stage:\s*([0-9.eE+-]+)", txt)
+    if not m or not t or m.group(1) != kernel_source_sha():
+        return None
+    return float(t.group(1))
+
+
+# ----------------------------------------------------------------------------- oracle baseline
+def oracle_mcups(variants, inst, budget_s: float, steps_cap: int = 100000):
+    """The FP64 oracle, as it stands, on one instance of each kind, RK2."""
+    import oracle
+    oracle.build()
+    picked = {}
+    for key, tau, u0 in inst:
+        picked.setdefault(key[0], (key, tau, u0))
+    runs = []
+    for key, tau, u0 in picked.values():
+        m = variants[key]
+        o = oracle.Oracle(m)
+        o.set_equilibrium(1.0, u0)
+        dt = o.cfl_dt(0.5, max(0.1, abs(u0[0])), tau, "rk2")
+        runs.append((o, m.n_cell, tau, dt))
+    cells = sum(r[1] for r in runs)
+    steps = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s and steps < steps_cap:
+        for o, _, tau, dt in runs:
+            o.run("rk2", tau, dt, 1)
+        steps += 1
+    el = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"{len(runs)} instances ({'+'.join(k for k in picked)}, {cells} cells), "
+              f"{steps} RK2 steps each, {el:.1f} s")
+    return cells * steps / el / 1e6, threads, sample, el, steps, cells
+
+
+# ----------------------------------------------------------------------------- arms
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    small = args.workload == "batch256-small"
+    variants, inst = batch_instances(256, small=small)
+    import oracle
+    oracle.build()
+    picked = {}
+    for key, tau, u0 in inst:
+        picked.setdefault(key[0], (key, tau, u0))
+    runs = []
+    for key, tau, u0 in picked.values():
+        o = oracle.Oracle(variants[key])
+        o.set_equilibrium(1.0, u0)
+        runs.append((o, variants[key].n_cell, tau, o.cfl_dt(0.5, max(0.1, abs(u0[0])), tau, "rk2")))
+    cells = sum(r[1] for r in runs)
+    for _ in range(args.warmup):
+        for o, _, tau, dt in runs:
+            o.run("rk2", tau, dt, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for o, _, tau, dt in runs:
+            o.run("rk2", tau, dt, 1)
+    el = time.perf_counter() - t0
+    v = cells * args.steps / el / 1e6
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = f"one instance of each kind ({cells} cells) per step, RK2"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MCUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "sample": sample, "scheme": "rk2"},
+            "cpu_baseline": {"value": v, "unit": "MCUPS", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "MCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = local if torch.cuda.is_available() else 0
+    torch.cuda.set_device(dev)
+
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1812_00390_gb300 import fvlbm as fv
+
+    small = args.workload == "batch256-small"
+    variants, inst = batch_instances(args.instances, small=small)
+
+    # CPU oracle baseline first (rank 0 only), before any GPU work
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        v, thr, sample, _, _, _ = oracle_mcups(variants, inst, args.cpu_seconds)
+        cpu = {"value": v, "unit": "MCUPS", "cores": thr, "kind": "oracle", "sample": sample}
+
+    s32, handles = build_solver(fv, variants, inst, "fp32")
+    n_cells = s32.n_cell
+    stream = s32.stream
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def timed(solver, k):
+        solver.step(args.warmup)
+        solver.sync()
+        barrier()
+        with ClockSampler(dev) as clk:
+            start.record(stream)
+            for _ in range(k):
+                solver.step(1)
+            end.record(stream)
+            end.synchronize()
+        ms = start.elapsed_time(end)
+        solver.sync()
+        barrier()
+        if dist is not None:
+            t = torch.tensor([ms], device=f"cuda:{dev}", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, clk.summary()
+
+    ms32, clocks = timed(s32, args.steps)
+    value = n_cells * world * args.steps / (ms32 / 1e3) / 1e6
+
+    # per-kernel device times (events around each launch)
+    kern_ms, _ = s32.profile(args.steps)
+    launches = s32.launches_per_step() * args.steps
+
+    # FP64 on the same workload, and the mixed-mode error against it
+    ms64 = None
+    err = None
+    if not args.no_fp64:
+        k64 = max(3, args.steps // 4)
+        s64, _ = build_solver(fv, variants, inst, "fp64", handles=handles)
+        ms64, _ = timed(s64, k64)
+        ms64 /= k64
+        # same number of steps from Step 0 in both modes
+        n_cmp = args.warmup + args.steps + args.steps
+        s64.close()
+        s64, _ = build_solver(fv, variants, inst, "fp64", handles=handles)
+        s64.step(n_cmp)
+        _, u64 = s64.macros()
+        s64.close()
+        ref32, _ = build_solver(fv, variants, inst, "fp32", handles=handles)
+        ref32.step(n_cmp)
+        _, u32 = ref32.macros()
+        ref32.close()
+        err = float(np.abs(u32 - u64).max() / np.abs(u64).max())
+        err_steps = n_cmp
+
+    # roofline of the stage kernels: algorithmic f traffic per RK2 stage,
+    # stage 1 reads f0 and writes f1, stage 2 reads f1 and f0 and writes f
+    bytes_store = 4
+    alg_per_cell_stage = (2 + 3) * 9 * bytes_store / 2.0        # 90 B, mean over the 2 stages
+    stage_ms = float(kern_ms[0] + kern_ms[1])
+    achieved = alg_per_cell_stage * n_cells / (stage_ms / 1e3) / 1e9
+    peak, peak_src = measured_peaks()
+    traffic_pc = ncu_traffic(args.workload)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": (traffic_pc * n_cells if traffic_pc else None),
+            "kernel": "one RK2 stage = face_values + update",
+            "kernel_ms": {"face_values": float(kern_ms[0]), "update": float(kern_ms[1])},
+            "algorithmic_bytes_per_launch": alg_per_cell_stage * n_cells,
+            "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+            else f"{peak_src} {HBM_FALLBACK_GBS:.0f} GB/s"}
+
+    # end to end through the C ABI with host buffers: each e2e step uploads the
+    # state from host memory, advances e2e_inner time steps, reads back the
+    # per-instance residual
+    f_host = s32.get_f()
+    e2e_inner = args.e2e_inner
+    s32.sync()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        s32.set_f(f_host)
+        s32.step(e2e_inner)
+        s32.residual()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = n_cells * world * e2e_inner * args.e2e_steps / e2e_s / 1e6
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MCUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "n_instances": args.instances, "n_cells": n_cells,
+                       "scheme": "rk2", "precision": "fp32 deviation (g = f - w)",
+                       "l2": "inputs larger than L2 (f state %.0f MB per GPU)" % (n_cells * 9 * 4 / 1e6),
+                       "parallelism": "instances replicated per GPU (weak scaling)" if world > 1 else "1 GPU"},
+            "fp64": {"value": (n_cells * world / (ms64 / 1e3) / 1e6) if ms64 else None, "unit": "MCUPS",
+                     "ms_per_step": ms64},
+            "mixed_over_fp64": (value / (n_cells * world / (ms64 / 1e3) / 1e6)) if ms64 else None,
+            "mixed_error_vs_fp64": ({"max_rel_velocity": err, "steps": err_steps} if err is not None else None),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": "MCUPS", "h2d_bytes_per_step": n_cells * 9 * 8,
+                    "d2h_bytes_per_step": 8 * args.instances + 4,
+                    "definition": f"set_f from host + {e2e_inner} time steps + residual read-back"},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batch256", choices=["batch256", "batch256-small"])
+    ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-inner", type=int, default=100)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

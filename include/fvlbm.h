@@ -159,8 +159,10 @@ int fvlbm_mesh_info(const fvlbm_mesh* mesh, fvlbm_mesh_info_t* info);
 
 /*
  * Time step of Eqs. (CFL) and (timetau) for instance `instance`:
- *   dt = cfl * min_cells(A / (Lx + Ly)) / (sqrt(2) + u_max), capped at 2 tau
- * (tau for AB2, the paper's observed limit).  Lx, Ly are the cell's extents.
+ *   dt = cfl * min( min_cells(A / (Lx + Ly)) / (sqrt(2) + u_max), 2 tau )
+ * (tau in place of 2 tau for AB2, the paper's observed limit).  Lx, Ly are the
+ * cell's extents.  The CFL number scales both limits, so neither is met with
+ * equality.
  * Writes *dt (host).  Errors: FVLBM_ERR_ARG.
  */
 int fvlbm_suggest_dt(const fvlbm_mesh* mesh, int32_t instance, double tau, double cfl,
@@ -226,6 +228,20 @@ int fvlbm_sync(fvlbm_solver* s);
 
 /* Time step in use for instance k (host, written). */
 int fvlbm_get_dt(const fvlbm_solver* s, int32_t instance, double* dt);
+
+/*
+ * Measurement aid: run n time steps like fvlbm_step, with a CUDA event pair
+ * around every kernel launch, and report the mean device time of each kernel
+ * kind in milliseconds.  Kinds, in order: [0] face-value kernel (Steps 1-3),
+ * [1] update kernel (Steps 4-5).  avg_ms: host [max_kinds] (max_kinds >= 2);
+ * n_kinds, launches (kernels launched): host, written.  Synchronises.
+ * Errors: FVLBM_ERR_ARG, _CUDA.
+ */
+int fvlbm_profile(fvlbm_solver* s, int64_t n, double* avg_ms, int32_t max_kinds, int32_t* n_kinds,
+                  int64_t* launches);
+
+/* Kernels one time step launches (host, written). */
+int fvlbm_launches_per_step(const fvlbm_solver* s, int64_t* launches);
 
 void fvlbm_solver_destroy(fvlbm_solver* s);
 

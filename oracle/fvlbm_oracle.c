@@ -574,10 +574,13 @@ int orc_run(void *hv, int scheme, double tau, double dt, int64_t nsteps) {
 }
 
 /*
- * Time step of Eqs. (CFL) and (timetau): dt = CFL * min_c(A_c/(Lx_c+Ly_c)) /
- * (|e|_max + |U|_max), capped at 2 tau for Euler and RK schemes and at tau for
- * AB2 (the paper's observed AB2 limit).  Lx, Ly are the cell's projected
- * lengths (bounding-box extents); the minimum is taken over all cells.
+ * Time step of Eqs. (CFL) and (timetau).  Both are stability limits: the
+ * advective one dt <= L / (|e|_max + |U|_max), L = min_c A_c/(Lx_c+Ly_c) over
+ * all cells (Lx, Ly the cell's projected lengths), and the collision one
+ * dt <= 2 tau (tau for AB2, the paper's observed AB2 limit).  The chosen step
+ * is the CFL number times the smaller of the two, so that neither limit is
+ * met with equality (at dt = 2 tau the relaxation factor of Euler and of the
+ * 2-stage scheme has modulus exactly 1).
  */
 double orc_cfl_dt(void *hv, double cfl, double umax, double tau, int scheme) {
     Oracle *h = (Oracle *)hv;
@@ -586,7 +589,7 @@ double orc_cfl_dt(void *hv, double cfl, double umax, double tau, int scheme) {
         double l = h->area[c] / (h->lx[c] + h->ly[c]);
         if (l < lmin) lmin = l;
     }
-    double dt = cfl * lmin / (sqrt(2.0) + umax);
-    double cap = scheme == S_AB2 ? tau : 2.0 * tau;
-    return dt < cap ? dt : cap;
+    double adv = lmin / (sqrt(2.0) + umax);
+    double col = scheme == S_AB2 ? tau : 2.0 * tau;
+    return cfl * (adv < col ? adv : col);
 }

@@ -59,8 +59,10 @@ def build(force: bool = False, verbose: bool = False, extra: tuple = ()) -> str:
             cmd = [nvcc, "-c", src, "-o", obj, "-O3", "-std=c++17", *ARCH, "-lineinfo",
                    "-Xcompiler", "-fPIC", "-Xptxas", "-O3", *inc, *extra]
         else:
+            # strict IEEE evaluation of the FP64 geometry (no FMA contraction), so
+            # that x86 and Arm hosts produce the same bits
             cmd = ["g++", "-c", src, "-o", obj, "-O2", "-std=c++17", "-fPIC", "-Wall",
-                   f"-I{cuda}/include", *inc]
+                   "-ffp-contract=off", f"-I{cuda}/include", *inc]
         jobs.append((cmd, obj))
 
     def run(cmd):

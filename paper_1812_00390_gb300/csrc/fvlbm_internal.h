@@ -64,8 +64,9 @@ struct Mesh {
 struct InstParam {
     double tau, inv_tau, dt;
     float inv_tau_f, dt_f;
-    float scale[FVLBM_Q];      // FP16 storage: stored = g * scale
+    float scale[FVLBM_Q];      // 16-bit storage: stored = (g - off) * scale
     float inv_scale[FVLBM_Q];
+    float off[FVLBM_Q];        // 16-bit storage offset: f^eq(rho0, u0) - w
     double rho0, u0x, u0y;
 };
 
@@ -113,8 +114,12 @@ struct DevView {
 
 // Kernel launchers (fvlbm_kernels.cu).  prec = fvlbm_precision.
 int launch_init_eq(const DevView& v, int prec, void* stream);
+// ev: null, or 3 cudaEvent_t recorded before the face-value kernel, between
+// the two kernels and after the update kernel.
 int launch_stage(const DevView& v, int prec, void* stream, const void* fin, const void* fbase,
-                 void* fout, double beta, int mode);
+                 void* fout, double beta, int mode, void* const* ev = nullptr);
+// Kernels launched by one stage.
+constexpr int STAGE_KERNELS = 2;
 int launch_macros(const DevView& v, int prec, void* stream);
 int launch_reduce(const DevView& v, void* stream, int what);
 int launch_get_f(const DevView& v, int prec, void* stream);

@@ -38,21 +38,33 @@ __device__ __forceinline__ T wgt(int a) {
 
 // ------------------------------------------------------------------ storage
 template <typename S> struct Store;
+// FP64 / FP32 keep the value itself.
 template <> struct Store<double> {
-    __device__ static double ld(const double* p, int64_t i, float) { return p[i]; }
-    __device__ static void st(double* p, int64_t i, double v, float) { p[i] = v; }
+    __device__ static double ld(const double* p, int64_t i, float, float) { return p[i]; }
+    __device__ static void st(double* p, int64_t i, double v, float, float) { p[i] = v; }
 };
 template <> struct Store<float> {
-    __device__ static float ld(const float* p, int64_t i, float) { return p[i]; }
-    __device__ static void st(float* p, int64_t i, float v, float) { p[i] = v; }
+    __device__ static float ld(const float* p, int64_t i, float, float) { return p[i]; }
+    __device__ static void st(float* p, int64_t i, float v, float, float) { p[i] = v; }
 };
+// 16-bit storage keeps (g - off) * scale: off is the deviation of the
+// instance's initial equilibrium, so the stored number is the departure from
+// it and the format's relative precision applies to that departure.
 template <> struct Store<__half> {
-    __device__ static float ld(const __half* p, int64_t i, float inv_scale) { return __half2float(p[i]) * inv_scale; }
-    __device__ static void st(__half* p, int64_t i, float v, float scale) { p[i] = __float2half_rn(v * scale); }
+    __device__ static float ld(const __half* p, int64_t i, float inv_scale, float off) {
+        return fmaf(__half2float(p[i]), inv_scale, off);
+    }
+    __device__ static void st(__half* p, int64_t i, float v, float scale, float off) {
+        p[i] = __float2half_rn((v - off) * scale);
+    }
 };
 template <> struct Store<__nv_bfloat16> {
-    __device__ static float ld(const __nv_bfloat16* p, int64_t i, float) { return __bfloat162float(p[i]); }
-    __device__ static void st(__nv_bfloat16* p, int64_t i, float v, float) { p[i] = __float2bfloat16_rn(v); }
+    __device__ static float ld(const __nv_bfloat16* p, int64_t i, float, float off) {
+        return __bfloat162float(p[i]) + off;
+    }
+    __device__ static void st(__nv_bfloat16* p, int64_t i, float v, float, float off) {
+        p[i] = __float2bfloat16_rn(v - off);
+    }
 };
 
 template <typename T> __device__ __forceinline__ T inst_dt(const InstParam& p);
@@ -63,30 +75,38 @@ template <> __device__ __forceinline__ double inst_inv_tau<double>(const InstPar
 template <> __device__ __forceinline__ float inst_inv_tau<float>(const InstParam& p) { return p.inv_tau_f; }
 
 // ------------------------------------------------------------------ physics
-// rho, u from f (FP64 mode) or from g = f - w (deviation mode): Sec. 2.1.
+// Density and velocity (Sec. 2.1).  FP64 mode: r = rho = sum f.  Deviation
+// mode: r = rho - 1 = sum g, kept unrounded by the 1 so that the density
+// deviation keeps FP32 relative precision.
 template <typename T, bool DEV>
-__device__ __forceinline__ void moments(const T* f, T& rho, T& ux, T& uy) {
-    T r = 0, mx = 0, my = 0;
+__device__ __forceinline__ void moments(const T* f, T& r, T& ux, T& uy) {
+    T s = 0, mx = 0, my = 0;
 #pragma unroll
     for (int a = 0; a < FVLBM_Q; a++) {
-        r += f[a];
+        s += f[a];
         mx += T(EXA(a)) * f[a];
         my += T(EYA(a)) * f[a];
     }
-    rho = DEV ? T(1) + r : r;
+    r = s;
+    const T rho = DEV ? T(1) + s : s;
     ux = mx / rho;
     uy = my / rho;
 }
 
-// Eq. (feq); in deviation mode returns f^eq - w.
+// Eq. (feq).  FP64 mode: r = rho, returns f^eq.  Deviation mode: r = rho - 1,
+// returns f^eq - w = w [(rho - 1) + rho (3 e.u + 4.5 (e.u)^2 - 1.5 u^2)].
 template <typename T, bool DEV>
-__device__ __forceinline__ T feqs(int a, T rho, T ux, T uy) {
+__device__ __forceinline__ T feqs(int a, T r, T ux, T uy) {
     T eu = T(EXA(a)) * ux + T(EYA(a)) * uy;
     T uu = ux * ux + uy * uy;
     T poly = T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu;
-    if (DEV) return wgt<T>(a) * ((rho - T(1)) + rho * poly);
-    return rho * wgt<T>(a) * (T(1) + poly);
+    if (DEV) return wgt<T>(a) * (r + (T(1) + r) * poly);
+    return r * wgt<T>(a) * (T(1) + poly);
 }
+
+// Density argument of feqs for a given density.
+template <typename T, bool DEV>
+__device__ __forceinline__ T rarg(double rho) { return DEV ? T(rho - 1.0) : T(rho); }
 
 // Stencil value minus the cell value for a boundary slot (Sec. 2.4.1):
 //   wall      f^eq(rho, u_w) - f^eq(rho, u)                        Eq. (wallbc)
@@ -98,8 +118,8 @@ __device__ __forceinline__ T bc_delta(uint32_t kind, const BcParam& b, int a, T 
                                       T nhx, T nhy) {
     switch (kind) {
         case SK_WALL: return feqs<T, DEV>(a, rho, T(b.uwx), T(b.uwy)) - fe;
-        case SK_INLET: return feqs<T, DEV>(a, b.external ? T(b.rho_inf) : rho, T(b.uix), T(b.uiy)) - fe;
-        case SK_OUTLET: return b.external ? T(0) : feqs<T, DEV>(a, T(b.rho_inf), ux, uy) - fe;
+        case SK_INLET: return feqs<T, DEV>(a, b.external ? rarg<T, DEV>(b.rho_inf) : rho, T(b.uix), T(b.uiy)) - fe;
+        case SK_OUTLET: return b.external ? T(0) : feqs<T, DEV>(a, rarg<T, DEV>(b.rho_inf), ux, uy) - fe;
         default: {  // symmetry
             T un = ux * nhx + uy * nhy;
             return feqs<T, DEV>(a, rho, ux - T(2) * un * nhx, uy - T(2) * un * nhy) - fa;
@@ -124,7 +144,7 @@ __global__ void __launch_bounds__(256) face_values_kernel(DevView v, const S* __
 
     T f[FVLBM_Q];
 #pragma unroll
-    for (int a = 0; a < FVLBM_Q; a++) f[a] = Store<S>::ld(fin, a * np + i, P.inv_scale[a]);
+    for (int a = 0; a < FVLBM_Q; a++) f[a] = Store<S>::ld(fin, a * np + i, P.inv_scale[a], P.off[a]);
     T rho, ux, uy;
     moments<T, DEV>(f, rho, ux, uy);
 
@@ -142,7 +162,7 @@ __global__ void __launch_bounds__(256) face_values_kernel(DevView v, const S* __
             const int64_t j = v.nbr[k * np + i];
 #pragma unroll
             for (int a = 1; a < FVLBM_Q; a++) {
-                T d = Store<S>::ld(fin, a * np + j, P.inv_scale[a]) - f[a];
+                T d = Store<S>::ld(fin, a * np + j, P.inv_scale[a], P.off[a]) - f[a];
                 gx[a - 1] += cx * d;
                 gy[a - 1] += cy * d;
             }
@@ -206,7 +226,7 @@ __global__ void __launch_bounds__(256) update_kernel(DevView v, const S* __restr
 
     T f[FVLBM_Q];
 #pragma unroll
-    for (int a = 0; a < FVLBM_Q; a++) f[a] = Store<S>::ld(fin, a * np + i, P.inv_scale[a]);
+    for (int a = 0; a < FVLBM_Q; a++) f[a] = Store<S>::ld(fin, a * np + i, P.inv_scale[a], P.off[a]);
     T rho, ux, uy;
     moments<T, DEV>(f, rho, ux, uy);
 
@@ -222,7 +242,12 @@ __global__ void __launch_bounds__(256) update_kernel(DevView v, const S* __restr
 #pragma unroll
         for (int a = 1; a < FVLBM_Q; a++) {
             const T en = T(EXA(a)) * nx + T(EYA(a)) * ny;
-            flux[a] += en * fv[(a - 1) * v.n_face + fid];
+            // deviation mode: the face vectors of a closed cell sum to zero, so
+            // subtracting the cell value leaves the flux unchanged in exact
+            // arithmetic and removes the rounding of the FP32 face vectors
+            // from the constant part of g
+            const T face = fv[(a - 1) * v.n_face + fid];
+            flux[a] += en * (DEV ? face - f[a] : face);
         }
     }
     const T inv_tau = inst_inv_tau<T>(P);
@@ -234,7 +259,7 @@ __global__ void __launch_bounds__(256) update_kernel(DevView v, const S* __restr
         const T rhs = -flux[a] - (f[a] - feqs<T, DEV>(a, rho, ux, uy)) * inv_tau;
         T out;
         if (mode == MODE_RK) {
-            const T base = (fbase == fin) ? f[a] : Store<S>::ld(fbase, a * np + i, P.inv_scale[a]);
+            const T base = (fbase == fin) ? f[a] : Store<S>::ld(fbase, a * np + i, P.inv_scale[a], P.off[a]);
             out = base + beta * dt * rhs;
         } else if (mode == MODE_AB2_FIRST) {
             out = f[a] + dt * rhs;
@@ -244,7 +269,7 @@ __global__ void __launch_bounds__(256) update_kernel(DevView v, const S* __restr
             rp[a * np + i] = rhs;
         }
         bad |= !finite_val(out);
-        Store<S>::st(fout, a * np + i, out, P.scale[a]);
+        Store<S>::st(fout, a * np + i, out, P.scale[a], P.off[a]);
     }
     if (bad) *v.flag = 1;
 }
@@ -257,7 +282,7 @@ __global__ void init_eq_kernel(DevView v) {
     const InstParam& P = v.inst[v.grp[i]];
     S* f = (S*)v.fa;
     for (int a = 0; a < FVLBM_Q; a++)
-        Store<S>::st(f, a * v.np + i, feqs<T, DEV>(a, T(P.rho0), T(P.u0x), T(P.u0y)), P.scale[a]);
+        Store<S>::st(f, a * v.np + i, feqs<T, DEV>(a, rarg<T, DEV>(P.rho0), T(P.u0x), T(P.u0y)), P.scale[a], P.off[a]);
 }
 
 // rho, u in FP64 from the stored state (Step 6).
@@ -269,7 +294,7 @@ __global__ void macros_kernel(DevView v) {
     const S* f = (const S*)v.fa;
     double r = 0, mx = 0, my = 0;
     for (int a = 0; a < FVLBM_Q; a++) {
-        double x = (double)Store<S>::ld(f, a * v.np + i, P.inv_scale[a]);
+        double x = (double)Store<S>::ld(f, a * v.np + i, P.inv_scale[a], P.off[a]);
         r += x;
         mx += EXA(a) * x;
         my += EYA(a) * x;
@@ -288,7 +313,7 @@ __global__ void get_f_kernel(DevView v) {
     const InstParam& P = v.inst[v.grp[i]];
     const S* f = (const S*)v.fa;
     for (int a = 0; a < FVLBM_Q; a++) {
-        double x = (double)Store<S>::ld(f, a * v.np + i, P.inv_scale[a]);
+        double x = (double)Store<S>::ld(f, a * v.np + i, P.inv_scale[a], P.off[a]);
         v.conv[a * v.np + i] = DEV ? x + wgt<double>(a) : x;
     }
 }
@@ -301,7 +326,7 @@ __global__ void set_f_kernel(DevView v) {
     S* f = (S*)v.fa;
     for (int a = 0; a < FVLBM_Q; a++) {
         double x = v.conv[a * v.np + i];
-        Store<S>::st(f, a * v.np + i, (T)(DEV ? x - wgt<double>(a) : x), P.scale[a]);
+        Store<S>::st(f, a * v.np + i, (T)(DEV ? x - wgt<double>(a) : x), P.scale[a], P.off[a]);
     }
 }
 
@@ -360,15 +385,17 @@ static int check_launch(const char* what) {
 
 template <typename T, typename S, bool DEV>
 static int stage_t(const DevView& v, cudaStream_t st, const void* fin, const void* fbase, void* fout,
-                   double beta, int mode) {
+                   double beta, int mode, void* const* ev) {
     const unsigned g = grid_of(v.n_cell, 256);
-    if (v.maxf == 4) {
-        face_values_kernel<T, S, 4, DEV><<<g, 256, 0, st>>>(v, (const S*)fin);
+    if (ev) cudaEventRecord((cudaEvent_t)ev[0], st);
+    if (v.maxf == 4) face_values_kernel<T, S, 4, DEV><<<g, 256, 0, st>>>(v, (const S*)fin);
+    else face_values_kernel<T, S, 8, DEV><<<g, 256, 0, st>>>(v, (const S*)fin);
+    if (ev) cudaEventRecord((cudaEvent_t)ev[1], st);
+    if (v.maxf == 4)
         update_kernel<T, S, 4, DEV><<<g, 256, 0, st>>>(v, (const S*)fin, (const S*)fbase, (S*)fout, (T)beta, mode);
-    } else {
-        face_values_kernel<T, S, 8, DEV><<<g, 256, 0, st>>>(v, (const S*)fin);
+    else
         update_kernel<T, S, 8, DEV><<<g, 256, 0, st>>>(v, (const S*)fin, (const S*)fbase, (S*)fout, (T)beta, mode);
-    }
+    if (ev) cudaEventRecord((cudaEvent_t)ev[2], st);
     return check_launch("stage kernels");
 }
 
@@ -382,9 +409,9 @@ static int stage_t(const DevView& v, cudaStream_t st, const void* fin, const voi
     }
 
 int launch_stage(const DevView& v, int prec, void* stream, const void* fin, const void* fbase, void* fout,
-                 double beta, int mode) {
+                 double beta, int mode, void* const* ev) {
     cudaStream_t st = (cudaStream_t)stream;
-    DISPATCH_PREC(prec, return (stage_t<T, S, DEV>(v, st, fin, fbase, fout, beta, mode)));
+    DISPATCH_PREC(prec, return (stage_t<T, S, DEV>(v, st, fin, fbase, fout, beta, mode, ev)));
 }
 
 int launch_init_eq(const DevView& v, int prec, void* stream) {

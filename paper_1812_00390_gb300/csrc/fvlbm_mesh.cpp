@@ -426,10 +426,12 @@ extern "C" int fvlbm_mesh_info(const fvlbm_mesh* mesh, fvlbm_mesh_info_t* info) 
 }
 
 namespace fvlbm {
+// CFL number times the smaller of the advective limit of Eq. (CFL) and the
+// collision limit of Eq. (timetau) (tau for AB2).
 double suggest_dt(const Mesh& M, int inst, double tau, double cfl, double umax, int scheme) {
-    double dt = cfl * M.inst_cfl_len[inst] / (std::sqrt(2.0) + umax);
-    double cap = scheme == FVLBM_AB2 ? tau : 2.0 * tau;
-    return dt < cap ? dt : cap;
+    double adv = M.inst_cfl_len[inst] / (std::sqrt(2.0) + umax);
+    double col = scheme == FVLBM_AB2 ? tau : 2.0 * tau;
+    return cfl * (adv < col ? adv : col);
 }
 }  // namespace fvlbm
 

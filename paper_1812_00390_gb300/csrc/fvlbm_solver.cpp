@@ -255,17 +255,25 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
         I.u0x = p.u0[0];
         I.u0y = p.u0[1];
         for (int a = 0; a < FVLBM_Q; a++) {
-            float sc = 1.0f;
+            const double w = a == 0 ? 4.0 / 9 : (a < 5 ? 1.0 / 9 : 1.0 / 36);
+            const double ex = a == 1 || a == 5 || a == 8 ? 1 : (a == 3 || a == 6 || a == 7 ? -1 : 0);
+            const double ey = a == 2 || a == 5 || a == 6 ? 1 : (a == 4 || a == 7 || a == 8 ? -1 : 0);
+            float sc = 1.0f, off = 0.0f;
+            if (p.precision == FVLBM_FP16_DEV || p.precision == FVLBM_BF16_DEV) {
+                // offset: deviation of the initial equilibrium f^eq(rho0, u0) - w (Eq. feq)
+                const double eu = ex * p.u0[0] + ey * p.u0[1], uu = p.u0[0] * p.u0[0] + p.u0[1] * p.u0[1];
+                off = (float)(w * ((p.rho0 - 1.0) + p.rho0 * (3 * eu + 4.5 * eu * eu - 1.5 * uu)));
+            }
             if (p.precision == FVLBM_FP16_DEV) {
-                // power-of-two scale that maps the expected |g_a| bound to ~2^12
-                const double w = a == 0 ? 4.0 / 9 : (a < 5 ? 1.0 / 9 : 1.0 / 36);
+                // power-of-two scale mapping a bound of |g - off| to ~2^12
                 const double e = a == 0 ? 0.0 : (a < 5 ? 1.0 : std::sqrt(2.0));
                 const double U = std::max(umax, 1e-3);
-                const double gmax = w * (0.1 + 1.1 * (3 * e * U + 4.5 * e * e * U * U + 1.5 * U * U));
+                const double gmax = w * (0.1 + 2.2 * (3 * e * U + 4.5 * e * e * U * U + 1.5 * U * U));
                 sc = std::ldexp(1.0f, (int)std::floor(std::log2(4096.0 / gmax)));
             }
             I.scale[a] = sc;
             I.inv_scale[a] = 1.0f / sc;
+            I.off[a] = off;
         }
     }
 
@@ -400,32 +408,84 @@ extern "C" int fvlbm_init(const fvlbm_mesh* mesh, const fvlbm_params* params, in
     return FVLBM_OK;
 }
 
-static int enqueue_step(fvlbm_solver* s) {
+// Stages per time step of each scheme.
+static int n_stages(int scheme) { return scheme == FVLBM_RK2 ? 2 : scheme == FVLBM_RK4 ? 4 : 1; }
+
+// Enqueue one time step.  ev: null, or 3 events per stage (see launch_stage).
+static int enqueue_step(fvlbm_solver* s, void* const* ev = nullptr) {
     const DevView& v = s->v;
     switch (s->scheme) {
         case FVLBM_EULER:
-            return launch_stage(v, s->prec, s->stream, v.fa, v.fa, v.fa, 1.0, MODE_RK);
+            return launch_stage(v, s->prec, s->stream, v.fa, v.fa, v.fa, 1.0, MODE_RK, ev);
         case FVLBM_RK2: {
-            int rc = launch_stage(v, s->prec, s->stream, v.fa, v.fa, v.fb, 0.5, MODE_RK);
-            return rc ? rc : launch_stage(v, s->prec, s->stream, v.fb, v.fa, v.fa, 1.0, MODE_RK);
+            int rc = launch_stage(v, s->prec, s->stream, v.fa, v.fa, v.fb, 0.5, MODE_RK, ev);
+            return rc ? rc : launch_stage(v, s->prec, s->stream, v.fb, v.fa, v.fa, 1.0, MODE_RK, ev ? ev + 3 : ev);
         }
         case FVLBM_RK4: {
             static const double beta[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
             for (int k = 0; k < 4; k++) {
                 int rc = launch_stage(v, s->prec, s->stream, k == 0 ? v.fa : v.fb, v.fa, k == 3 ? v.fa : v.fb,
-                                      beta[k], MODE_RK);
+                                      beta[k], MODE_RK, ev ? ev + 3 * k : ev);
                 if (rc) return rc;
             }
             return FVLBM_OK;
         }
         case FVLBM_AB2: {
             int rc = launch_stage(v, s->prec, s->stream, v.fa, v.fa, v.fa, 1.0,
-                                  s->ab2_started ? MODE_AB2 : MODE_AB2_FIRST);
+                                  s->ab2_started ? MODE_AB2 : MODE_AB2_FIRST, ev);
             s->ab2_started = true;
             return rc;
         }
     }
     return fail(FVLBM_ERR_ARG, "bad scheme");
+}
+
+extern "C" int fvlbm_profile(fvlbm_solver* s, int64_t n, double* avg_ms, int32_t max_kinds, int32_t* n_kinds,
+                             int64_t* launches) {
+    clear_error();
+    if (!s || n <= 0 || !avg_ms || max_kinds < STAGE_KERNELS || !n_kinds || !launches)
+        return fail(FVLBM_ERR_ARG, "fvlbm_profile: bad arguments");
+    DeviceGuard dg(s->device);
+    const int ns = n_stages(s->scheme);
+    std::vector<cudaEvent_t> ev((size_t)3 * ns * n, nullptr);
+    int rc = FVLBM_OK;
+    for (auto& e : ev) {
+        cudaError_t ce = cudaEventCreate(&e);
+        if (ce != cudaSuccess) {
+            e = nullptr;
+            rc = cuda_fail(ce, "fvlbm_profile: event");
+            break;
+        }
+    }
+    for (int64_t k = 0; k < n && rc == FVLBM_OK; k++) rc = enqueue_step(s, (void* const*)&ev[(size_t)3 * ns * k]);
+    if (rc == FVLBM_OK) {
+        cudaError_t ce = cudaStreamSynchronize(s->stream);
+        if (ce != cudaSuccess) rc = cuda_fail(ce, "fvlbm_profile: synchronise");
+    }
+    if (rc == FVLBM_OK) {
+        double t[STAGE_KERNELS] = {0, 0};
+        for (size_t q = 0; q < ev.size(); q += 3) {
+            float a = 0, b = 0;
+            cudaEventElapsedTime(&a, ev[q], ev[q + 1]);
+            cudaEventElapsedTime(&b, ev[q + 1], ev[q + 2]);
+            t[0] += a;
+            t[1] += b;
+        }
+        const double launches_per_kind = (double)ns * n;
+        for (int q = 0; q < STAGE_KERNELS; q++) avg_ms[q] = t[q] / launches_per_kind;
+        *n_kinds = STAGE_KERNELS;
+        *launches = (int64_t)STAGE_KERNELS * ns * n;
+    }
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
+    return rc;
+}
+
+extern "C" int fvlbm_launches_per_step(const fvlbm_solver* s, int64_t* launches) {
+    clear_error();
+    if (!s || !launches) return fail(FVLBM_ERR_ARG, "fvlbm_launches_per_step: null argument");
+    *launches = (int64_t)STAGE_KERNELS * n_stages(s->scheme);
+    return FVLBM_OK;
 }
 
 extern "C" int fvlbm_step(fvlbm_solver* s, int64_t n) {

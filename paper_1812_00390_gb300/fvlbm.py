@@ -56,7 +56,8 @@ class MeshInfoT(C.Structure):
 EXPORTS = ["fvlbm_mesh_create", "fvlbm_mesh_concat", "fvlbm_mesh_destroy", "fvlbm_mesh_info",
            "fvlbm_suggest_dt", "fvlbm_workspace_bytes", "fvlbm_init", "fvlbm_step", "fvlbm_macros",
            "fvlbm_residual", "fvlbm_mass", "fvlbm_get_f", "fvlbm_set_f", "fvlbm_sync",
-           "fvlbm_get_dt", "fvlbm_solver_destroy", "fvlbm_last_error"]
+           "fvlbm_get_dt", "fvlbm_profile", "fvlbm_launches_per_step", "fvlbm_solver_destroy",
+           "fvlbm_last_error"]
 
 
 def _load():
@@ -86,6 +87,8 @@ def _load():
         "fvlbm_set_f": [P, dp],
         "fvlbm_sync": [P],
         "fvlbm_get_dt": [P, C.c_int32, dp],
+        "fvlbm_profile": [P, C.c_int64, dp, C.c_int32, i32p, i64p],
+        "fvlbm_launches_per_step": [P, i64p],
         "fvlbm_solver_destroy": [P],
         "fvlbm_last_error": [],
     }
@@ -257,6 +260,19 @@ class Solver:
         d = C.c_double()
         _check(lib.fvlbm_get_dt(self._h, instance, C.byref(d)))
         return d.value
+
+    def profile(self, n: int):
+        """Mean device ms of each kernel kind over n steps, and kernels launched."""
+        ms = np.zeros(8)
+        nk = C.c_int32()
+        nl = C.c_int64()
+        _check(lib.fvlbm_profile(self._h, int(n), _d(ms), 8, C.byref(nk), C.byref(nl)))
+        return ms[:nk.value].copy(), nl.value
+
+    def launches_per_step(self) -> int:
+        n = C.c_int64()
+        _check(lib.fvlbm_launches_per_step(self._h, C.byref(n)))
+        return n.value
 
     def close(self):
         h = getattr(self, "_h", None)

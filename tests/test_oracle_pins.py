@@ -64,7 +64,7 @@ def test_equilibrium_moments(orc):
 # --------------------------------------------------------------------------- geometry / dt
 def test_geometry_and_cfl_dt(orc):
     """Right triangles of legs h: A = h^2/2, centroid = vertex mean, and the CFL
-    rule of Eqs. (CFL), (timetau) gives dt = CFL (h/4) / (sqrt2 + U), capped at 2 tau."""
+    rule of Eqs. (CFL), (timetau) gives dt = CFL min((h/4) / (sqrt2 + U), 2 tau)."""
     h = 0.5
     m = mg.couette(nx=4, ny=3, h=h, jitter=0.0)
     o = orc.Oracle(m)
@@ -75,8 +75,8 @@ def test_geometry_and_cfl_dt(orc):
         np.testing.assert_allclose(c[k], m.xy[v].mean(0), atol=1e-15)
     np.testing.assert_allclose(l, h, rtol=1e-15)
     assert abs(o.cfl_dt(0.5, 0.1, 10.0, "euler") - 0.5 * (h / 4) / (np.sqrt(2) + 0.1)) < 1e-15
-    assert o.cfl_dt(0.5, 0.1, 1e-3, "euler") == 2e-3
-    assert o.cfl_dt(0.5, 0.1, 1e-3, "ab2") == 1e-3
+    assert o.cfl_dt(0.5, 0.1, 1e-3, "euler") == 0.5 * 2e-3
+    assert o.cfl_dt(0.5, 0.1, 1e-3, "ab2") == 0.5 * 1e-3
     # quads of a stretched cavity: shoelace area sums to the domain area
     mq = mg.cavity(8, ratio=5.0)
     aq, cq, _ = orc.Oracle(mq).geometry()
