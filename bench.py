@@ -98,7 +98,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
@@ -300,14 +300,14 @@ def run_ours(args):
     value = n_cells * world * args.steps / (ms32 / 1e3) / 1e6
 
     # per-kernel device times (events around each launch)
-    kern_ms, _ = s32.profile(args.steps)
+    kern_ms, _ = s32.profile(max(3, args.steps // 4))
     launches = s32.launches_per_step() * args.steps
 
     # FP64 on the same workload, and the mixed-mode error against it
     ms64 = None
     err = None
     if not args.no_fp64:
-        k64 = max(3, args.steps // 4)
+        k64 = max(3, args.steps // 8)
         s64, _ = build_solver(fv, variants, inst, "fp64", handles=handles)
         ms64, _ = timed(s64, k64)
         ms64 /= k64
@@ -387,8 +387,8 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch256", choices=["batch256", "batch256-small"])
     ap.add_argument("--instances", type=int, default=256)

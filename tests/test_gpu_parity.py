@@ -195,7 +195,7 @@ def test_cavity_fp32_velocity_error(fv, orc):
     assert err < 1e-5, err
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp16", 1e-2), ("bf16", 0.2)])
+@pytest.mark.parametrize("prec,tol", [("fp32", 5e-6), ("fp16", 1e-2), ("bf16", 0.2)])
 def test_deviation_modes_error_bound(fv, orc, prec, tol):
     """Stored-precision error after 500 RK2 steps of a cylinder hybrid mesh (far
     field, wall), relative to the largest velocity."""
