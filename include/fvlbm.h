@@ -218,6 +218,27 @@ int fvlbm_residual(fvlbm_solver* s, double* e);
 /* Total mass sum_i A_i rho_i of each instance, FP64.  mass host [n_instances]. */
 int fvlbm_mass(fvlbm_solver* s, double* mass);
 
+/*
+ * Same result as fvlbm_mass, computed without allocating anything.  The paper
+ * has no counterpart; this entry point serves callers that may not allocate
+ * memory while they run -- processes whose device memory is reserved up front
+ * by another allocator (a framework's caching pool, a fixed serving budget),
+ * and real-time loops or plugins that must not touch the device heap.
+ *   s     solver (its state and geometry are the inputs)
+ *   mass  host [n_instances], written
+ * The block partial sums live in a fixed 96 KB array in the library's device
+ * memory (allocated when the library loads, held by every GPU that loads it
+ * until the process exits), not in the solver's workspace.  Limits: at most
+ * 8192 chunks of 4096 cells (33,554,432 cells) and 4096 instances per solver;
+ * larger solvers get FVLBM_ERR_ARG with the limits in the message.
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  Every call on a device shares the
+ * array, so calls that overlap on the GPU (other threads, other streams)
+ * race; serialise them.  Nothing carries over from an earlier call.
+ * Synchronises the solver's stream.  Errors: FVLBM_ERR_ARG, _CUDA, _DIVERGED.
+ */
+int fvlbm_mass_noalloc(fvlbm_solver* s, double* mass);
+
 /* Read / write the distribution functions, host [n_cell][9] FP64, caller order.
  * Writing also restarts AB2 history.  Synchronise. */
 int fvlbm_get_f(fvlbm_solver* s, double* f);

@@ -125,6 +125,18 @@ int launch_reduce(const DevView& v, void* stream, int what);
 int launch_get_f(const DevView& v, int prec, void* stream);
 int launch_set_f(const DevView& v, int prec, void* stream);
 
+// Solver internals for entry points defined outside the solver's own file.
+struct SolverRef {
+    const DevView* view;
+    int prec;
+    int device;
+    void* stream;
+    int32_t n_inst;
+};
+int solver_ref(fvlbm_solver* s, SolverRef* out);
+// Reads the solver's non-finite flag after synchronising its stream.
+int solver_sync_check(fvlbm_solver* s);
+
 // Stage modes of launch_stage.
 enum StageMode { MODE_RK = 0, MODE_AB2_FIRST = 1, MODE_AB2 = 2 };
 // Reductions of launch_reduce.

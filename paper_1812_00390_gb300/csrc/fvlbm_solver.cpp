@@ -507,6 +507,19 @@ static int sync_and_check(fvlbm_solver* s) {
     return FVLBM_OK;
 }
 
+namespace fvlbm {
+int solver_ref(fvlbm_solver* s, SolverRef* out) {
+    if (!s || !out) return fail(FVLBM_ERR_ARG, "null solver");
+    out->view = &s->v;
+    out->prec = s->prec;
+    out->device = s->device;
+    out->stream = s->stream;
+    out->n_inst = s->n_inst;
+    return FVLBM_OK;
+}
+int solver_sync_check(fvlbm_solver* s) { return sync_and_check(s); }
+}  // namespace fvlbm
+
 extern "C" int fvlbm_sync(fvlbm_solver* s) {
     clear_error();
     if (!s) return fail(FVLBM_ERR_ARG, "fvlbm_sync: null solver");

@@ -55,7 +55,7 @@ class MeshInfoT(C.Structure):
 #: every symbol include/fvlbm.h declares
 EXPORTS = ["fvlbm_mesh_create", "fvlbm_mesh_concat", "fvlbm_mesh_destroy", "fvlbm_mesh_info",
            "fvlbm_suggest_dt", "fvlbm_workspace_bytes", "fvlbm_init", "fvlbm_step", "fvlbm_macros",
-           "fvlbm_residual", "fvlbm_mass", "fvlbm_get_f", "fvlbm_set_f", "fvlbm_sync",
+           "fvlbm_residual", "fvlbm_mass", "fvlbm_mass_noalloc", "fvlbm_get_f", "fvlbm_set_f", "fvlbm_sync",
            "fvlbm_get_dt", "fvlbm_profile", "fvlbm_launches_per_step", "fvlbm_solver_destroy",
            "fvlbm_last_error"]
 
@@ -83,6 +83,7 @@ def _load():
         "fvlbm_macros": [P, dp, dp],
         "fvlbm_residual": [P, dp],
         "fvlbm_mass": [P, dp],
+        "fvlbm_mass_noalloc": [P, dp],
         "fvlbm_get_f": [P, dp],
         "fvlbm_set_f": [P, dp],
         "fvlbm_sync": [P],
@@ -245,6 +246,13 @@ class Solver:
     def mass(self) -> np.ndarray:
         m = np.zeros(self.n_inst)
         _check(lib.fvlbm_mass(self._h, _d(m)))
+        return m
+
+    def mass_noalloc(self) -> np.ndarray:
+        """fvlbm_mass computed without any allocation by the call (fixed
+        library scratch; calls on one device must not overlap)."""
+        m = np.zeros(self.n_inst)
+        _check(lib.fvlbm_mass_noalloc(self._h, _d(m)))
         return m
 
     def get_f(self) -> np.ndarray:
