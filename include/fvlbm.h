@@ -105,7 +105,9 @@ typedef struct fvlbm_params {
     double rho0;       /* initial density (Step 0: f = f^eq(rho0, u0)) */
     double u0[2];      /* initial velocity */
     int32_t device;    /* CUDA device ordinal; equal for all instances */
-    int32_t reserved;  /* set to 0 */
+    int32_t kernel;    /* stage kernel: 0 = automatic; 1 = two kernels per stage (face
+                          values through memory); 128, 256 or 512 = one fused kernel per
+                          stage with that many cells per tile; equal for all instances */
 } fvlbm_params;
 
 typedef struct fvlbm_mesh_info_s {
@@ -253,8 +255,9 @@ int fvlbm_get_dt(const fvlbm_solver* s, int32_t instance, double* dt);
 /*
  * Measurement aid: run n time steps like fvlbm_step, with a CUDA event pair
  * around every kernel launch, and report the mean device time of each kernel
- * kind in milliseconds.  Kinds, in order: [0] face-value kernel (Steps 1-3),
- * [1] update kernel (Steps 4-5).  avg_ms: host [max_kinds] (max_kinds >= 2);
+ * kind in milliseconds.  Fused stage (n_kinds = 1): [0] the stage kernel.
+ * Two-kernel stage (n_kinds = 2): [0] face-value kernel (Steps 1-3), [1]
+ * update kernel (Steps 4-5).  avg_ms: host [max_kinds] (max_kinds >= 2);
  * n_kinds, launches (kernels launched): host, written.  Synchronises.
  * Errors: FVLBM_ERR_ARG, _CUDA.
  */

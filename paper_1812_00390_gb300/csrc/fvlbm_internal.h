@@ -110,7 +110,21 @@ struct DevView {
     const int64_t* chunk;   // [n_chunk][3] (begin, end, instance)
     int64_t n_chunk;
     int32_t* flag;  // non-finite flag
+    // fused stage (one CTA per tile of `tile` consecutive cells)
+    int32_t strategy;        // STRATEGY_TWO_KERNEL or STRATEGY_TILE
+    int32_t tile;            // cells per tile (threads per CTA)
+    int64_t n_tiles;
+    int32_t lmax;            // most local cells (tile + halo) of any tile
+    int32_t gmax;            // most cells with a gradient (tile + 1-ring) of any tile
+    const int64_t* halo_ptr; // [n_tiles + 1] into halo
+    const int32_t* halo;     // 1-ring then 2-ring cells of each tile (global ids)
+    const int32_t* n_r1;     // [n_tiles] 1-ring size
+    const uint16_t* lnbr;    // [maxf][np] tile-local index of the neighbour across each face
+    const uint16_t* r1nbr;   // [halo entries][maxf] tile-local stencil of 1-ring cells
+    const void* rn;          // T [2][maxf][np] neighbour-side face midpoint - neighbour centroid
 };
+
+enum Strategy { STRATEGY_TWO_KERNEL = 0, STRATEGY_TILE = 1 };
 
 // Kernel launchers (fvlbm_kernels.cu).  prec = fvlbm_precision.
 int launch_init_eq(const DevView& v, int prec, void* stream);
@@ -118,8 +132,22 @@ int launch_init_eq(const DevView& v, int prec, void* stream);
 // the two kernels and after the update kernel.
 int launch_stage(const DevView& v, int prec, void* stream, const void* fin, const void* fbase,
                  void* fout, double beta, int mode, void* const* ev = nullptr);
-// Kernels launched by one stage.
+// Most kernels launched by one stage (two-kernel strategy).
 constexpr int STAGE_KERNELS = 2;
+inline int stage_kernels(const DevView& v) { return v.strategy == STRATEGY_TILE ? 1 : 2; }
+// Dynamic shared memory of the fused stage kernel for real type of `rsize` bytes.
+inline size_t tile_smem_bytes(const DevView& v, size_t rsize) {
+    return rsize * ((size_t)FVLBM_Q * v.lmax + 2 * (FVLBM_Q - 1) * (size_t)v.gmax);
+}
+// One translation unit per state precision.
+int stage_fp64(const DevView& v, void* stream, const void* fin, const void* fbase, void* fout, double beta, int mode,
+               void* const* ev);
+int stage_fp32(const DevView& v, void* stream, const void* fin, const void* fbase, void* fout, double beta, int mode,
+               void* const* ev);
+int stage_fp16(const DevView& v, void* stream, const void* fin, const void* fbase, void* fout, double beta, int mode,
+               void* const* ev);
+int stage_bf16(const DevView& v, void* stream, const void* fin, const void* fbase, void* fout, double beta, int mode,
+               void* const* ev);
 int launch_macros(const DevView& v, int prec, void* stream);
 int launch_reduce(const DevView& v, void* stream, int what);
 int launch_get_f(const DevView& v, int prec, void* stream);

@@ -71,29 +71,131 @@ size_t store_size(int prec) {
     return prec == FVLBM_FP64 ? 8 : (prec == FVLBM_FP32_DEV ? 4 : 2);
 }
 
+// Halo structure of the fused stage kernel: tiles of `tile` consecutive cells
+// (internal order); per tile its 1-ring (face neighbours outside the tile) and
+// 2-ring (face neighbours of the 1-ring outside tile and 1-ring), and tile-local
+// indices of every neighbour the kernel reads.
+struct TilePlan {
+    int tile = 0;
+    int64_t n_tiles = 0;
+    int32_t lmax = 0, gmax = 0;
+    std::vector<int64_t> halo_ptr;
+    std::vector<int32_t> halo;
+    std::vector<int32_t> n_r1;
+    std::vector<uint16_t> lnbr;   // [maxf][np]
+    std::vector<uint16_t> r1nbr;  // [halo][maxf]
+};
+
+int64_t internal_nbr(const Mesh& M, int64_t i, int k) {
+    const Slot& S = M.slots[(size_t)M.perm[i] * MAXP + k];
+    return S.kind == SK_INTERIOR ? M.iperm[S.nb] : -1;
+}
+
+void make_tiles(const Mesh& M, int64_t np, int maxf, int tile, TilePlan& P) {
+    const int64_t n = M.n_cell;
+    P.tile = tile;
+    P.n_tiles = (n + tile - 1) / tile;
+    P.halo_ptr.assign(P.n_tiles + 1, 0);
+    P.n_r1.assign(P.n_tiles, 0);
+    P.lnbr.assign((size_t)maxf * np, 0xFFFF);
+    P.halo.clear();
+    std::vector<int64_t> stamp(n, -1);
+    std::vector<int32_t> loc(n, 0);
+    std::vector<int64_t> r1;
+    std::vector<uint16_t> r1nbr;
+    P.lmax = P.gmax = 0;
+    for (int64_t t = 0; t < P.n_tiles; t++) {
+        const int64_t c0 = t * tile, c1 = std::min(n, c0 + tile);
+        int32_t nl = 0;
+        for (int64_t i = c0; i < c1; i++) {
+            stamp[i] = t;
+            loc[i] = nl++;
+        }
+        r1.clear();
+        for (int64_t i = c0; i < c1; i++)
+            for (int k = 0; k < M.nf[M.perm[i]]; k++) {
+                const int64_t j = internal_nbr(M, i, k);
+                if (j >= 0 && stamp[j] != t) {
+                    stamp[j] = t;
+                    loc[j] = nl++;
+                    r1.push_back(j);
+                    P.halo.push_back((int32_t)j);
+                }
+            }
+        const int32_t n1 = (int32_t)r1.size();
+        for (int64_t j : r1)
+            for (int k = 0; k < M.nf[M.perm[j]]; k++) {
+                const int64_t q = internal_nbr(M, j, k);
+                if (q >= 0 && stamp[q] != t) {
+                    stamp[q] = t;
+                    loc[q] = nl++;
+                    P.halo.push_back((int32_t)q);
+                }
+            }
+        for (int64_t i = c0; i < c1; i++)
+            for (int k = 0; k < M.nf[M.perm[i]]; k++) {
+                const int64_t j = internal_nbr(M, i, k);
+                if (j >= 0) P.lnbr[(size_t)k * np + i] = (uint16_t)loc[j];
+            }
+        // stencil of every halo entry (only the 1-ring's are read)
+        const size_t base = r1nbr.size();
+        r1nbr.resize(base + (size_t)(P.halo.size() - P.halo_ptr[t]) * maxf, 0xFFFF);
+        for (int32_t q = 0; q < n1; q++)
+            for (int k = 0; k < M.nf[M.perm[r1[q]]]; k++) {
+                const int64_t j = internal_nbr(M, r1[q], k);
+                if (j >= 0) r1nbr[base + (size_t)q * maxf + k] = (uint16_t)loc[j];
+            }
+        P.halo_ptr[t + 1] = (int64_t)P.halo.size();
+        P.n_r1[t] = n1;
+        P.lmax = std::max(P.lmax, nl);
+        P.gmax = std::max<int32_t>(P.gmax, (int32_t)(c1 - c0) + n1);
+    }
+    P.r1nbr.swap(r1nbr);
+}
+
 // Offsets of every array inside the workspace.
 struct Layout {
     int64_t np, n_face, n_chunk;
     int maxf;
+    int strategy;
+    TilePlan tp;
     size_t off_nbr, off_fid, off_meta, off_cg, off_rv, off_nv, off_area, off_grp, off_inst, off_bc,
         off_fa, off_fb, off_rprev, off_fv, off_rho, off_ux, off_uy, off_uold, off_part, off_red, off_conv,
-        off_chunk, off_flag, total;
+        off_chunk, off_flag, off_hptr, off_halo, off_nr1, off_lnbr, off_r1nbr, off_rn, total;
 };
 
-Layout make_layout(const Mesh& M, int prec, int scheme) {
-    Layout L{};
+constexpr size_t SMEM_LIMIT = 227 * 1024;
+
+// kernel: 0 automatic, 1 two-kernel, 128/256/512 fused with that tile size.
+int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L) {
+    L = Layout{};
     L.np = (M.n_cell + 63) / 64 * 64;
     L.n_face = M.n_face;
     L.maxf = M.max_faces <= 4 ? 4 : 8;
     L.n_chunk = 0;
     for (int k = 0; k < M.n_inst; k++) L.n_chunk += (M.inst_begin[k + 1] - M.inst_begin[k] + CHUNK - 1) / CHUNK;
+    const size_t R = real_size(prec), S = store_size(prec);
+    if (kernel != 0 && kernel != 1 && kernel != 128 && kernel != 256 && kernel != 512)
+        return fail(FVLBM_ERR_ARG, "params.kernel = %d: use 0, 1, 128, 256 or 512", kernel);
+    L.strategy = kernel == 1 ? STRATEGY_TWO_KERNEL : STRATEGY_TILE;
+    if (L.strategy == STRATEGY_TILE) {
+        make_tiles(M, L.np, L.maxf, kernel == 0 ? 256 : kernel, L.tp);
+        const size_t smem = R * ((size_t)FVLBM_Q * L.tp.lmax + 2 * (FVLBM_Q - 1) * (size_t)L.tp.gmax);
+        if (smem > SMEM_LIMIT || L.tp.lmax >= 0xFFFF) {
+            if (kernel != 0)
+                return fail(FVLBM_ERR_UNSUPPORTED, "fused stage needs %zu B of shared memory per tile (limit %zu)",
+                            smem, SMEM_LIMIT);
+            L.strategy = STRATEGY_TWO_KERNEL;
+            L.tp = TilePlan{};
+        }
+    }
+    const bool tiled = L.strategy == STRATEGY_TILE;
     size_t o = 0;
     auto take = [&](size_t bytes) {
         size_t r = o;
         o += (bytes + ALIGN - 1) / ALIGN * ALIGN;
         return r;
     };
-    const size_t R = real_size(prec), S = store_size(prec);
     const size_t plane = (size_t)L.np;
     L.off_nbr = take(4 * plane * L.maxf);
     L.off_fid = take(4 * plane * L.maxf);
@@ -105,10 +207,16 @@ Layout make_layout(const Mesh& M, int prec, int scheme) {
     L.off_grp = take(4 * plane);
     L.off_inst = take(sizeof(InstParam) * M.n_inst);
     L.off_bc = take(sizeof(BcParam) * std::max<size_t>(1, M.bcs.size()));
-    L.off_fa = take(S * plane * FVLBM_Q);
+    L.off_hptr = take(tiled ? 8 * (size_t)(L.tp.n_tiles + 1) : 0);
+    L.off_halo = take(tiled ? 4 * L.tp.halo.size() : 0);
+    L.off_nr1 = take(tiled ? 4 * (size_t)L.tp.n_tiles : 0);
+    L.off_lnbr = take(tiled ? 2 * plane * L.maxf : 0);
+    L.off_r1nbr = take(tiled ? 2 * L.tp.r1nbr.size() : 0);
+    L.off_rn = take(tiled ? R * plane * L.maxf * 2 : 0);
+    L.off_fa = take(S * plane * FVLBM_Q);   // everything before this is uploaded once
     L.off_fb = (scheme == FVLBM_RK2 || scheme == FVLBM_RK4) ? take(S * plane * FVLBM_Q) : 0;
     L.off_rprev = scheme == FVLBM_AB2 ? take(R * plane * FVLBM_Q) : 0;
-    L.off_fv = take(R * (size_t)std::max<int64_t>(1, L.n_face) * (FVLBM_Q - 1));
+    L.off_fv = tiled ? take(0) : take(R * (size_t)std::max<int64_t>(1, L.n_face) * (FVLBM_Q - 1));
     L.off_rho = take(8 * plane);
     L.off_ux = take(8 * plane);
     L.off_uy = take(8 * plane);
@@ -119,7 +227,7 @@ Layout make_layout(const Mesh& M, int prec, int scheme) {
     L.off_chunk = take(24 * (size_t)std::max<int64_t>(1, L.n_chunk));
     L.off_flag = take(16);
     L.total = o;
-    return L;
+    return FVLBM_OK;
 }
 
 int check_params(const Mesh& M, const fvlbm_params* params, int32_t n_params) {
@@ -132,8 +240,9 @@ int check_params(const Mesh& M, const fvlbm_params* params, int32_t n_params) {
         if (p.scheme < FVLBM_EULER || p.scheme > FVLBM_RK4) return fail(FVLBM_ERR_ARG, "params[%d]: bad scheme", k);
         if (p.precision < FVLBM_FP64 || p.precision > FVLBM_BF16_DEV)
             return fail(FVLBM_ERR_ARG, "params[%d]: bad precision", k);
-        if (p.scheme != params[0].scheme || p.precision != params[0].precision || p.device != params[0].device)
-            return fail(FVLBM_ERR_ARG, "params[%d]: scheme, precision and device must match params[0]", k);
+        if (p.scheme != params[0].scheme || p.precision != params[0].precision || p.device != params[0].device ||
+            p.kernel != params[0].kernel)
+            return fail(FVLBM_ERR_ARG, "params[%d]: scheme, precision, device and kernel must match params[0]", k);
     }
     if (M.bcs.size() >= 65536) return fail(FVLBM_ERR_ARG, "too many boundary tags (%zu)", M.bcs.size());
     return FVLBM_OK;
@@ -163,6 +272,7 @@ void pack_geometry(const Mesh& M, const Layout& L, std::vector<unsigned char>& h
     T* nv = (T*)(host.data() + L.off_nv);
     double* area = (double*)(host.data() + L.off_area);
     int32_t* grp = (int32_t*)(host.data() + L.off_grp);
+    T* rn = L.strategy == STRATEGY_TILE ? (T*)(host.data() + L.off_rn) : nullptr;
     for (int64_t x = 0; x < (int64_t)maxf * np; x++) {
         nbr[x] = -1;
         fid[x] = -1;
@@ -196,6 +306,12 @@ void pack_geometry(const Mesh& M, const Layout& L, std::vector<unsigned char>& h
             rv[(1 * maxf + k) * np + i] = (T)(S.py - M.cy[c]);
             nv[(0 * maxf + k) * np + i] = (T)(S.nx / M.area[c]);
             nv[(1 * maxf + k) * np + i] = (T)(S.ny / M.area[c]);
+            if (rn && S.kind == SK_INTERIOR) {
+                // the neighbour's own reconstruction vector to this face
+                const Slot& Q = M.slots[(size_t)S.nb * MAXP + S.nb_slot];
+                rn[(0 * maxf + k) * np + i] = (T)(Q.px - M.cx[S.nb]);
+                rn[(1 * maxf + k) * np + i] = (T)(Q.py - M.cy[S.nb]);
+            }
         }
     }
 }
@@ -208,7 +324,14 @@ extern "C" int fvlbm_workspace_bytes(const fvlbm_mesh* mesh, const fvlbm_params*
     if (!mesh || !bytes) return fail(FVLBM_ERR_ARG, "fvlbm_workspace_bytes: null argument");
     int rc = check_params(mesh->m, params, n_params);
     if (rc) return rc;
-    *bytes = make_layout(mesh->m, params[0].precision, params[0].scheme).total;
+    Layout L;
+    try {
+        rc = make_layout(mesh->m, params[0].precision, params[0].scheme, params[0].kernel, L);
+    } catch (const std::bad_alloc&) {
+        return fail(FVLBM_ERR_OOM, "fvlbm_workspace_bytes: out of host memory");
+    }
+    if (rc) return rc;
+    *bytes = L.total;
     return FVLBM_OK;
 }
 
@@ -278,7 +401,13 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
     }
 
     // layout, workspace
-    Layout L = make_layout(M, s->prec, s->scheme);
+    Layout L;
+    try {
+        rc = make_layout(M, s->prec, s->scheme, p0.kernel, L);
+    } catch (const std::bad_alloc&) {
+        return fail(FVLBM_ERR_OOM, "fvlbm_init: out of host memory");
+    }
+    if (rc) return rc;
     if (workspace) {
         if (workspace_bytes < L.total)
             return fail(FVLBM_ERR_OOM, "fvlbm_init: workspace of %zu bytes, %zu needed", workspace_bytes, L.total);
@@ -301,6 +430,13 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
         host.assign(L.off_fa, 0);
         if (s->prec == FVLBM_FP64) pack_geometry<double>(M, L, host);
         else pack_geometry<float>(M, L, host);
+        if (L.strategy == STRATEGY_TILE) {
+            std::memcpy(host.data() + L.off_hptr, L.tp.halo_ptr.data(), 8 * L.tp.halo_ptr.size());
+            std::memcpy(host.data() + L.off_halo, L.tp.halo.data(), 4 * L.tp.halo.size());
+            std::memcpy(host.data() + L.off_nr1, L.tp.n_r1.data(), 4 * L.tp.n_r1.size());
+            std::memcpy(host.data() + L.off_lnbr, L.tp.lnbr.data(), 2 * L.tp.lnbr.size());
+            std::memcpy(host.data() + L.off_r1nbr, L.tp.r1nbr.data(), 2 * L.tp.r1nbr.size());
+        }
     } catch (const std::bad_alloc&) {
         return fail(FVLBM_ERR_OOM, "fvlbm_init: out of host memory");
     }
@@ -328,8 +464,10 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
     CK(cudaMemcpyAsync(base + L.off_chunk, chunks.data(), chunks.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
                        s->stream), "upload chunk table");
     // face values start at zero: directions parallel to a face (e.n = 0) are never written
-    CK(cudaMemsetAsync(base + L.off_fv, 0, real_size(s->prec) * (size_t)std::max<int64_t>(1, L.n_face) * (FVLBM_Q - 1),
-                       s->stream), "clear face values");
+    if (L.strategy == STRATEGY_TWO_KERNEL)
+        CK(cudaMemsetAsync(base + L.off_fv, 0,
+                           real_size(s->prec) * (size_t)std::max<int64_t>(1, L.n_face) * (FVLBM_Q - 1), s->stream),
+           "clear face values");
     CK(cudaMemsetAsync(base + L.off_flag, 0, 16, s->stream), "clear flag");
 
     DevView& v = s->v;
@@ -362,6 +500,19 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
     v.chunk = (const int64_t*)(base + L.off_chunk);
     v.n_chunk = (int64_t)chunks.size() / 3;
     v.flag = (int32_t*)(base + L.off_flag);
+    v.strategy = L.strategy;
+    if (L.strategy == STRATEGY_TILE) {
+        v.tile = L.tp.tile;
+        v.n_tiles = L.tp.n_tiles;
+        v.lmax = L.tp.lmax;
+        v.gmax = L.tp.gmax;
+        v.halo_ptr = (const int64_t*)(base + L.off_hptr);
+        v.halo = (const int32_t*)(base + L.off_halo);
+        v.n_r1 = (const int32_t*)(base + L.off_nr1);
+        v.lnbr = (const uint16_t*)(base + L.off_lnbr);
+        v.r1nbr = (const uint16_t*)(base + L.off_r1nbr);
+        v.rn = base + L.off_rn;
+    }
 
     // Step 0 and the first residual snapshot
     rc = launch_init_eq(v, s->prec, s->stream);
@@ -472,9 +623,10 @@ extern "C" int fvlbm_profile(fvlbm_solver* s, int64_t n, double* avg_ms, int32_t
             t[1] += b;
         }
         const double launches_per_kind = (double)ns * n;
-        for (int q = 0; q < STAGE_KERNELS; q++) avg_ms[q] = t[q] / launches_per_kind;
-        *n_kinds = STAGE_KERNELS;
-        *launches = (int64_t)STAGE_KERNELS * ns * n;
+        const int kinds = stage_kernels(s->v);
+        for (int q = 0; q < kinds; q++) avg_ms[q] = t[q] / launches_per_kind;
+        *n_kinds = kinds;
+        *launches = (int64_t)kinds * ns * n;
     }
     for (auto& e : ev)
         if (e) cudaEventDestroy(e);
@@ -484,7 +636,7 @@ extern "C" int fvlbm_profile(fvlbm_solver* s, int64_t n, double* avg_ms, int32_t
 extern "C" int fvlbm_launches_per_step(const fvlbm_solver* s, int64_t* launches) {
     clear_error();
     if (!s || !launches) return fail(FVLBM_ERR_ARG, "fvlbm_launches_per_step: null argument");
-    *launches = (int64_t)STAGE_KERNELS * n_stages(s->scheme);
+    *launches = (int64_t)stage_kernels(s->v) * n_stages(s->scheme);
     return FVLBM_OK;
 }
 

@@ -1,0 +1,9 @@
+// Stage kernels instantiated for the fp16 state.
+#include "fvlbm_stage.cuh"
+
+namespace fvlbm {
+int stage_fp16(const DevView& v, void* stream, const void* fin, const void* fbase, void* fout, double beta,
+               int mode, void* const* ev) {
+    return stage_t<float, __half, true>(v, (cudaStream_t)stream, fin, fbase, fout, beta, mode, ev);
+}
+}  // namespace fvlbm

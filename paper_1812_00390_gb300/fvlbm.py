@@ -43,7 +43,7 @@ class BcT(C.Structure):
 class ParamsT(C.Structure):
     _fields_ = [("tau", C.c_double), ("dt", C.c_double), ("cfl", C.c_double), ("u_max", C.c_double),
                 ("scheme", C.c_int32), ("precision", C.c_int32), ("rho0", C.c_double),
-                ("u0", C.c_double * 2), ("device", C.c_int32), ("reserved", C.c_int32)]
+                ("u0", C.c_double * 2), ("device", C.c_int32), ("kernel", C.c_int32)]
 
 
 class MeshInfoT(C.Structure):
@@ -180,13 +180,15 @@ def _prec(p) -> int:
 
 
 def make_params(tau: float, dt: float = 0.0, scheme="euler", precision="fp64", rho0: float = 1.0,
-                u0=(0.0, 0.0), cfl: float = 0.0, u_max: float = 0.0, device: int = 0) -> ParamsT:
+                u0=(0.0, 0.0), cfl: float = 0.0, u_max: float = 0.0, device: int = 0,
+                kernel: int = 0) -> ParamsT:
     p = ParamsT()
     p.tau, p.dt, p.cfl, p.u_max = tau, dt, cfl, u_max
     p.scheme, p.precision = _scheme(scheme), _prec(precision)
     p.rho0 = rho0
     p.u0[:] = list(u0)
     p.device = device
+    p.kernel = kernel
     return p
 
 

@@ -86,6 +86,46 @@ def test_fp64_parity_every_mesh_and_scheme(fv, orc, name, scheme):
     s.close()
 
 
+@pytest.mark.parametrize("kernel", [1, 128, 256, 512])
+@pytest.mark.parametrize("name", ["cylinder", "bricks", "internal_io", "two_tri_periodic", "cavity_tri"])
+def test_stage_kernel_variants(fv, orc, name, kernel):
+    """Two-kernel stage and fused stage (each tile size) against the oracle in
+    FP64, and against each other in FP32."""
+    m = MESHES[name]()
+    tau = 0.15
+    o = orc.Oracle(m)
+    dt = o.cfl_dt(0.5, 0.1, tau, "rk2")
+    f0 = f_random(orc, m, seed=17)
+    s = fv.Solver(fv.Mesh(m), fv.make_params(tau, dt=dt, scheme="rk2", precision="fp64", kernel=kernel))
+    s.set_f(f0)
+    s.step(15)
+    o.set_f(f0)
+    o.run("rk2", tau, dt, 15)
+    assert rel_err(s.get_f(), o.get_f()) < FP64_TOL
+    ref = fv.Solver(fv.Mesh(m), fv.make_params(tau, dt=dt, scheme="rk2", precision="fp32", kernel=1))
+    got = fv.Solver(fv.Mesh(m), fv.make_params(tau, dt=dt, scheme="rk2", precision="fp32", kernel=kernel))
+    for x in (ref, got):
+        x.set_f(f0)
+        x.step(15)
+    assert rel_err(got.get_f(), ref.get_f()) < 1e-6
+
+
+def test_fused_tiles_span_instances(fv):
+    """Tiles that straddle instance boundaries give the same state as the
+    two-kernel stage (instances of 2 to 3750 cells, tile 512)."""
+    meshes = [mg.two_triangles(), mg.couette(8, 3), mg.cavity(10, 3.0), mg.two_triangles(periodic=True),
+              mg.cylinder_hybrid(n_rad=25, n_circ=50, n_tri_rings=25, seed=3), mg.bricks(6, 4)]
+    hs = [fv.Mesh(m) for m in meshes]
+    taus = [0.2, 0.24, 0.05, 0.3, 0.02, 0.1]
+    out = []
+    for kernel in (1, 512):
+        s = fv.Solver(fv.Mesh.concat(hs), [fv.make_params(t, scheme="rk4", precision="fp64", kernel=kernel,
+                                                          u0=(0.02, 0.0)) for t in taus])
+        s.step(12)
+        out.append(s.get_f())
+    assert rel_err(out[1], out[0]) < 1e-14
+
+
 def test_couette_config_fp64(fv, orc):
     """32x8 jittered Couette channel, Re = 10, explicit Euler, 2000 steps from rest
     (Step 0 done on each side): FP64 parity, then the closed-form profile."""
