@@ -41,10 +41,13 @@ HBM_FALLBACK_GBS = 6800.0
 
 
 # ----------------------------------------------------------------------------- workload
-def batch_instances(n_inst: int, seed: int = 2018, small: bool = False):
-    """(meshgen meshes by variant, list of (variant key, tau, u0)) for the batch."""
+def batch_instances(n_inst: int, seed: int = 2018, small: bool = False, rank: int = 0):
+    """(meshgen meshes by variant, list of (variant key, tau, u0)) for the batch.
+
+    Rank r of a multi-GPU run solves its own batch (seed + r): the same mix and
+    cell count on every GPU, different Reynolds numbers (weak scaling)."""
     from paper_1812_00390_gb300 import meshgen as mg
-    specs = mg.batch_specs(n_inst, seed=seed)
+    specs = mg.batch_specs(n_inst, seed=seed + rank)
     variants = {}
     out = []
     for k, sp in enumerate(specs):
@@ -79,6 +82,17 @@ def build_solver(fv, variants, inst, precision, scheme="rk2", handles=None):
     mesh = fv.Mesh.concat([handles[k] for k, _, _ in inst])
     params = [fv.make_params(tau, scheme=scheme, precision=precision, u0=u0) for _, tau, u0 in inst]
     return fv.Solver(mesh, params), handles
+
+
+# ----------------------------------------------------------------------------- ranks
+def reduce_max(x: float, dist, device=None) -> float:
+    """Largest value over all ranks (the slowest rank's time); x itself at N = 1."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -259,7 +273,7 @@ def run_ours(args):
     from paper_1812_00390_gb300 import fvlbm as fv
 
     small = args.workload == "batch256-small"
-    variants, inst = batch_instances(args.instances, small=small)
+    variants, inst = batch_instances(args.instances, small=small, rank=rank)
 
     # CPU oracle baseline first (rank 0 only), before any GPU work
     cpu = None
@@ -290,10 +304,7 @@ def run_ours(args):
         ms = start.elapsed_time(end)
         solver.sync()
         barrier()
-        if dist is not None:
-            t = torch.tensor([ms], device=f"cuda:{dev}", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = reduce_max(ms, dist, f"cuda:{dev}")
         return ms, clk.summary()
 
     ms32, clocks = timed(s32, args.steps)

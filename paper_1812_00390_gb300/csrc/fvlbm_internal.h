@@ -37,6 +37,8 @@ struct Slot {
     double px = 0, py = 0;   // face midpoint
     double sx = 0, sy = 0;   // periodic: neighbour image = neighbour centroid + (sx, sy)
     double cgx = 0, cgy = 0; // least-squares coefficient of this slot's stencil point
+    double vx = 0, vy = 0;   // start vertex of the edge (the edge runs to the next slot's)
+    double sdx = 0, sdy = 0; // stencil point minus cell centroid
     uint32_t outmask = 0;    // bit a-1 set when e_a . n > 0 (a = 1..8): upwind side is this cell
 };
 
@@ -85,9 +87,10 @@ struct DevView {
     int32_t maxf;       // slots per cell in the packed arrays (4 or 8)
     int32_t n_inst;
     // geometry, [maxf][np] planes
+    const uint32_t* meta;  // kind | outmask << 8 | bc << 16
+    // two-kernel stage only
     const int32_t* nbr;
     const int32_t* fid;
-    const uint32_t* meta;  // kind | outmask << 8 | bc << 16
     const void* cg;        // T [2][maxf][np]   least-squares coefficients
     const void* rv;        // T [2][maxf][np]   face midpoint - centroid
     const void* nv;        // T [2][maxf][np]   (dy, -dx) / A
@@ -121,7 +124,10 @@ struct DevView {
     const int32_t* n_r1;     // [n_tiles] 1-ring size
     const uint16_t* lnbr;    // [maxf][np] tile-local index of the neighbour across each face
     const uint16_t* r1nbr;   // [halo entries][maxf] tile-local stencil of 1-ring cells
-    const void* rn;          // T [2][maxf][np] neighbour-side face midpoint - neighbour centroid
+    // compact geometry of the fused stage: everything else is derived in-kernel
+    const void* pg;          // T [2][maxf][np] start vertex of each face - centroid
+    const void* dg;          // T [2][maxf][np] least-squares stencil point - centroid
+    const void* ia;          // T [np] 1 / area
 };
 
 enum Strategy { STRATEGY_TWO_KERNEL = 0, STRATEGY_TILE = 1 };

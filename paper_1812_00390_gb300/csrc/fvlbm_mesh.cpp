@@ -125,6 +125,8 @@ static int build_single(const double* xy, int64_t n_vert, const int64_t* cell_pt
             S.ny = -(xb - xa);
             S.px = 0.5 * (xa + xb);
             S.py = 0.5 * (ya + yb);
+            S.vx = xa;
+            S.vy = ya;
         }
         if (!(a2 > 0))
             return fail(FVLBM_ERR_DEGENERATE_CELL, "cell %lld has non-positive area (vertices must be CCW)", (long long)c);
@@ -275,6 +277,8 @@ static int build_single(const double* xy, int64_t n_vert, const int64_t* cell_pt
                 yn = M.cy[c] + 2.0 * dn * ny;
             }
             double dx = xn - M.cx[c], dy = yn - M.cy[c];
+            M.slots[(size_t)c * MAXP + k].sdx = dx;
+            M.slots[(size_t)c * MAXP + k].sdy = dy;
             double w = 1.0 / (dx * dx + dy * dy);
             dxs[k] = w * dx;
             dys[k] = w * dy;

@@ -153,7 +153,7 @@ void make_tiles(const Mesh& M, int64_t np, int maxf, int tile, TilePlan& P) {
     P.r1nbr.swap(r1nbr);
 }
 
-// Offsets of every array inside the workspace.
+// Offsets of every array inside the workspace (0 size when a strategy does not use it).
 struct Layout {
     int64_t np, n_face, n_chunk;
     int maxf;
@@ -161,15 +161,17 @@ struct Layout {
     TilePlan tp;
     size_t off_nbr, off_fid, off_meta, off_cg, off_rv, off_nv, off_area, off_grp, off_inst, off_bc,
         off_fa, off_fb, off_rprev, off_fv, off_rho, off_ux, off_uy, off_uold, off_part, off_red, off_conv,
-        off_chunk, off_flag, off_hptr, off_halo, off_nr1, off_lnbr, off_r1nbr, off_rn, total;
+        off_chunk, off_flag, off_hptr, off_halo, off_nr1, off_lnbr, off_r1nbr, off_pg, off_dg, off_ia, total;
 };
 
 constexpr size_t SMEM_LIMIT = 227 * 1024;
+constexpr int64_t PLANE_ALIGN = 512;   // planes hold whole tiles of the largest tile size
 
-// kernel: 0 automatic, 1 two-kernel, 128/256/512 fused with that tile size.
+// kernel: 0 automatic (fused tile 256, except FP64: two kernels, which spend
+// fewer FP64 operations), 1 two-kernel, 128/256/512 fused with that tile size.
 int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L) {
     L = Layout{};
-    L.np = (M.n_cell + 63) / 64 * 64;
+    L.np = (M.n_cell + PLANE_ALIGN - 1) / PLANE_ALIGN * PLANE_ALIGN;
     L.n_face = M.n_face;
     L.maxf = M.max_faces <= 4 ? 4 : 8;
     L.n_chunk = 0;
@@ -177,7 +179,7 @@ int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L) {
     const size_t R = real_size(prec), S = store_size(prec);
     if (kernel != 0 && kernel != 1 && kernel != 128 && kernel != 256 && kernel != 512)
         return fail(FVLBM_ERR_ARG, "params.kernel = %d: use 0, 1, 128, 256 or 512", kernel);
-    L.strategy = kernel == 1 ? STRATEGY_TWO_KERNEL : STRATEGY_TILE;
+    L.strategy = (kernel == 1 || (kernel == 0 && prec == FVLBM_FP64)) ? STRATEGY_TWO_KERNEL : STRATEGY_TILE;
     if (L.strategy == STRATEGY_TILE) {
         make_tiles(M, L.np, L.maxf, kernel == 0 ? 256 : kernel, L.tp);
         const size_t smem = R * ((size_t)FVLBM_Q * L.tp.lmax + 2 * (FVLBM_Q - 1) * (size_t)L.tp.gmax);
@@ -189,34 +191,36 @@ int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L) {
             L.tp = TilePlan{};
         }
     }
-    const bool tiled = L.strategy == STRATEGY_TILE;
+    const bool tiled = L.strategy == STRATEGY_TILE, two = !tiled;
     size_t o = 0;
     auto take = [&](size_t bytes) {
         size_t r = o;
         o += (bytes + ALIGN - 1) / ALIGN * ALIGN;
         return r;
     };
-    const size_t plane = (size_t)L.np;
-    L.off_nbr = take(4 * plane * L.maxf);
-    L.off_fid = take(4 * plane * L.maxf);
-    L.off_meta = take(4 * plane * L.maxf);
-    L.off_cg = take(R * plane * L.maxf * 2);
-    L.off_rv = take(R * plane * L.maxf * 2);
-    L.off_nv = take(R * plane * L.maxf * 2);
+    const size_t plane = (size_t)L.np, slots = plane * L.maxf;
+    L.off_meta = take(4 * slots);
     L.off_area = take(8 * plane);
     L.off_grp = take(4 * plane);
     L.off_inst = take(sizeof(InstParam) * M.n_inst);
     L.off_bc = take(sizeof(BcParam) * std::max<size_t>(1, M.bcs.size()));
+    L.off_nbr = take(two ? 4 * slots : 0);
+    L.off_fid = take(two ? 4 * slots : 0);
+    L.off_cg = take(two ? R * slots * 2 : 0);
+    L.off_rv = take(two ? R * slots * 2 : 0);
+    L.off_nv = take(two ? R * slots * 2 : 0);
     L.off_hptr = take(tiled ? 8 * (size_t)(L.tp.n_tiles + 1) : 0);
     L.off_halo = take(tiled ? 4 * L.tp.halo.size() : 0);
     L.off_nr1 = take(tiled ? 4 * (size_t)L.tp.n_tiles : 0);
-    L.off_lnbr = take(tiled ? 2 * plane * L.maxf : 0);
+    L.off_lnbr = take(tiled ? 2 * slots : 0);
     L.off_r1nbr = take(tiled ? 2 * L.tp.r1nbr.size() : 0);
-    L.off_rn = take(tiled ? R * plane * L.maxf * 2 : 0);
+    L.off_pg = take(tiled ? R * slots * 2 : 0);
+    L.off_dg = take(tiled ? R * slots * 2 : 0);
+    L.off_ia = take(tiled ? R * plane : 0);
     L.off_fa = take(S * plane * FVLBM_Q);   // everything before this is uploaded once
     L.off_fb = (scheme == FVLBM_RK2 || scheme == FVLBM_RK4) ? take(S * plane * FVLBM_Q) : 0;
     L.off_rprev = scheme == FVLBM_AB2 ? take(R * plane * FVLBM_Q) : 0;
-    L.off_fv = tiled ? take(0) : take(R * (size_t)std::max<int64_t>(1, L.n_face) * (FVLBM_Q - 1));
+    L.off_fv = take(two ? R * (size_t)std::max<int64_t>(1, L.n_face) * (FVLBM_Q - 1) : 0);
     L.off_rho = take(8 * plane);
     L.off_ux = take(8 * plane);
     L.off_uy = take(8 * plane);
@@ -264,19 +268,22 @@ template <typename T>
 void pack_geometry(const Mesh& M, const Layout& L, std::vector<unsigned char>& host) {
     const int64_t n = M.n_cell, np = L.np;
     const int maxf = L.maxf;
-    int32_t* nbr = (int32_t*)(host.data() + L.off_nbr);
-    int32_t* fid = (int32_t*)(host.data() + L.off_fid);
-    uint32_t* meta = (uint32_t*)(host.data() + L.off_meta);
-    T* cg = (T*)(host.data() + L.off_cg);
-    T* rv = (T*)(host.data() + L.off_rv);
-    T* nv = (T*)(host.data() + L.off_nv);
-    double* area = (double*)(host.data() + L.off_area);
-    int32_t* grp = (int32_t*)(host.data() + L.off_grp);
-    T* rn = L.strategy == STRATEGY_TILE ? (T*)(host.data() + L.off_rn) : nullptr;
+    const bool two = L.strategy == STRATEGY_TWO_KERNEL;
+    unsigned char* H = host.data();
+    uint32_t* meta = (uint32_t*)(H + L.off_meta);
+    double* area = (double*)(H + L.off_area);
+    int32_t* grp = (int32_t*)(H + L.off_grp);
+    int32_t* nbr = two ? (int32_t*)(H + L.off_nbr) : nullptr;
+    int32_t* fid = two ? (int32_t*)(H + L.off_fid) : nullptr;
+    T* cg = two ? (T*)(H + L.off_cg) : nullptr;
+    T* rv = two ? (T*)(H + L.off_rv) : nullptr;
+    T* nv = two ? (T*)(H + L.off_nv) : nullptr;
+    T* pg = two ? nullptr : (T*)(H + L.off_pg);
+    T* dg = two ? nullptr : (T*)(H + L.off_dg);
+    T* ia = two ? nullptr : (T*)(H + L.off_ia);
     for (int64_t x = 0; x < (int64_t)maxf * np; x++) {
-        nbr[x] = -1;
-        fid[x] = -1;
         meta[x] = SK_NONE;
+        if (two) nbr[x] = fid[x] = -1;
     }
     int64_t next = 0;
     int32_t g = 0;
@@ -285,32 +292,34 @@ void pack_geometry(const Mesh& M, const Layout& L, std::vector<unsigned char>& h
         while (g + 1 < M.n_inst && c >= M.inst_begin[g + 1]) g++;
         grp[i] = g;
         area[i] = M.area[c];
+        if (ia) ia[i] = (T)(1.0 / M.area[c]);
         for (int k = 0; k < M.nf[c]; k++) {
             const Slot& S = M.slots[(size_t)c * MAXP + k];
             const int64_t x = (int64_t)k * np + i;
             meta[x] = (uint32_t)S.kind | (S.outmask << 8) | ((uint32_t)(S.bc < 0 ? 0 : S.bc) << 16);
-            if (S.kind == SK_INTERIOR) {
-                const int64_t j = M.iperm[S.nb];
-                nbr[x] = (int32_t)j;
-                if (fid[x] < 0) {
-                    fid[x] = (int32_t)next;
-                    fid[(int64_t)S.nb_slot * np + j] = (int32_t)next;
-                    next++;
+            if (two) {
+                if (S.kind == SK_INTERIOR) {
+                    const int64_t j = M.iperm[S.nb];
+                    nbr[x] = (int32_t)j;
+                    if (fid[x] < 0) {
+                        fid[x] = (int32_t)next;
+                        fid[(int64_t)S.nb_slot * np + j] = (int32_t)next;
+                        next++;
+                    }
+                } else {
+                    fid[x] = (int32_t)next++;
                 }
+                cg[(0 * maxf + k) * np + i] = (T)S.cgx;
+                cg[(1 * maxf + k) * np + i] = (T)S.cgy;
+                rv[(0 * maxf + k) * np + i] = (T)(S.px - M.cx[c]);
+                rv[(1 * maxf + k) * np + i] = (T)(S.py - M.cy[c]);
+                nv[(0 * maxf + k) * np + i] = (T)(S.nx / M.area[c]);
+                nv[(1 * maxf + k) * np + i] = (T)(S.ny / M.area[c]);
             } else {
-                fid[x] = (int32_t)next++;
-            }
-            cg[(0 * maxf + k) * np + i] = (T)S.cgx;
-            cg[(1 * maxf + k) * np + i] = (T)S.cgy;
-            rv[(0 * maxf + k) * np + i] = (T)(S.px - M.cx[c]);
-            rv[(1 * maxf + k) * np + i] = (T)(S.py - M.cy[c]);
-            nv[(0 * maxf + k) * np + i] = (T)(S.nx / M.area[c]);
-            nv[(1 * maxf + k) * np + i] = (T)(S.ny / M.area[c]);
-            if (rn && S.kind == SK_INTERIOR) {
-                // the neighbour's own reconstruction vector to this face
-                const Slot& Q = M.slots[(size_t)S.nb * MAXP + S.nb_slot];
-                rn[(0 * maxf + k) * np + i] = (T)(Q.px - M.cx[S.nb]);
-                rn[(1 * maxf + k) * np + i] = (T)(Q.py - M.cy[S.nb]);
+                pg[(0 * maxf + k) * np + i] = (T)(S.vx - M.cx[c]);
+                pg[(1 * maxf + k) * np + i] = (T)(S.vy - M.cy[c]);
+                dg[(0 * maxf + k) * np + i] = (T)S.sdx;
+                dg[(1 * maxf + k) * np + i] = (T)S.sdy;
             }
         }
     }
@@ -511,7 +520,9 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
         v.n_r1 = (const int32_t*)(base + L.off_nr1);
         v.lnbr = (const uint16_t*)(base + L.off_lnbr);
         v.r1nbr = (const uint16_t*)(base + L.off_r1nbr);
-        v.rn = base + L.off_rn;
+        v.pg = base + L.off_pg;
+        v.dg = base + L.off_dg;
+        v.ia = base + L.off_ia;
     }
 
     // Step 0 and the first residual snapshot

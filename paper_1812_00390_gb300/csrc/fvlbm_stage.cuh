@@ -214,6 +214,37 @@ __global__ void __launch_bounds__(256) update_kernel(DevView v, const S* __restr
     if (bad) *v.flag = 1;
 }
 
+// Geometry of one cell derived from its compact description (fused stage):
+// vertex offsets p_k (edge k runs from vertex k to vertex k+1) and stencil
+// offsets d_k, both relative to the centroid.  Face vector (dy, -dx) of each
+// edge, face midpoint offset, and least-squares coefficients
+// c_k = M^{-1} w_k d_k with M = sum_k w_k d_k d_k^T, w_k = 1/|d_k|^2
+// (Eq. leastsquare).
+template <typename T, int MAXF>
+__device__ __forceinline__ void lsq_coeffs(const T* dx, const T* dy, int nf, T* cx, T* cy) {
+    T m11 = 0, m12 = 0, m22 = 0;
+#pragma unroll
+    for (int k = 0; k < MAXF; k++) {
+        if (k < nf) {
+            const T w = T(1) / (dx[k] * dx[k] + dy[k] * dy[k]);
+            cx[k] = w * dx[k];
+            cy[k] = w * dy[k];
+            m11 += cx[k] * dx[k];
+            m12 += cx[k] * dy[k];
+            m22 += cy[k] * dy[k];
+        }
+    }
+    const T idet = T(1) / (m11 * m22 - m12 * m12);
+#pragma unroll
+    for (int k = 0; k < MAXF; k++) {
+        if (k < nf) {
+            const T a = cx[k], b = cy[k];
+            cx[k] = (m22 * a - m12 * b) * idet;
+            cy[k] = (m11 * b - m12 * a) * idet;
+        }
+    }
+}
+
 // Fused stage: one CTA per tile of TILE consecutive cells (Hilbert order).
 //   phase 1  f of the tile, its 1-ring and its 2-ring into shared memory
 //   phase 2  gradients (Eq. leastsquare) of the tile and 1-ring cells, kept in
@@ -239,10 +270,8 @@ __global__ void __launch_bounds__(TILE) stage_tile_kernel(DevView v, const S* __
     const int nh = (int)(v.halo_ptr[t + 1] - h0);
     const int n1 = v.n_r1[t];
     const int nl = nt + nh;
-    const T* cg = (const T*)v.cg;
-    const T* rv = (const T*)v.rv;
-    const T* rn = (const T*)v.rn;
-    const T* nv = (const T*)v.nv;
+    const T* pg = (const T*)v.pg;
+    const T* dg = (const T*)v.dg;
 
     // phase 1
     for (int l = threadIdx.x; l < nl; l += TILE) {
@@ -257,6 +286,17 @@ __global__ void __launch_bounds__(TILE) stage_tile_kernel(DevView v, const S* __
     for (int l = threadIdx.x; l < nt + n1; l += TILE) {
         const bool own = l < nt;
         const int64_t gi = own ? c0 + l : (int64_t)v.halo[h0 + l - nt];
+        uint32_t meta[MAXF];
+        T dx[MAXF], dy[MAXF], cx[MAXF], cy[MAXF];
+        int nf = 0;
+#pragma unroll
+        for (int k = 0; k < MAXF; k++) {
+            meta[k] = v.meta[k * np + gi];
+            dx[k] = dg[(0 * MAXF + k) * np + gi];
+            dy[k] = dg[(1 * MAXF + k) * np + gi];
+            nf += (meta[k] & 0xFF) != SK_NONE;
+        }
+        lsq_coeffs<T, MAXF>(dx, dy, nf, cx, cy);
         T f[FVLBM_Q];
 #pragma unroll
         for (int a = 0; a < FVLBM_Q; a++) f[a] = fs[a * lmax + l];
@@ -267,28 +307,32 @@ __global__ void __launch_bounds__(TILE) stage_tile_kernel(DevView v, const S* __
         for (int a = 0; a < FVLBM_Q - 1; a++) gx[a] = gy[a] = T(0);
 #pragma unroll
         for (int k = 0; k < MAXF; k++) {
-            const uint32_t meta = v.meta[k * np + gi];
-            const uint32_t kind = meta & 0xFF;
+            const uint32_t kind = meta[k] & 0xFF;
             if (kind == SK_NONE) continue;
-            const T cx = cg[(0 * MAXF + k) * np + gi], cy = cg[(1 * MAXF + k) * np + gi];
             if (kind == SK_INTERIOR) {
                 const int lj = own ? (int)v.lnbr[k * np + gi] : (int)v.r1nbr[(h0 + l - nt) * MAXF + k];
 #pragma unroll
                 for (int a = 1; a < FVLBM_Q; a++) {
                     const T d = fs[a * lmax + lj] - f[a];
-                    gx[a - 1] += cx * d;
-                    gy[a - 1] += cy * d;
+                    gx[a - 1] += cx[k] * d;
+                    gy[a - 1] += cy[k] * d;
                 }
             } else {
-                const BcParam& b = v.bc[meta >> 16];
-                const T nx = nv[(0 * MAXF + k) * np + gi], ny = nv[(1 * MAXF + k) * np + gi];
-                const T inv = T(1) / sqrt(nx * nx + ny * ny);
+                const BcParam& b = v.bc[meta[k] >> 16];
+                T nhx = 0, nhy = 0;
+                if (kind == SK_SYMMETRY) {
+                    const int k1 = (k + 1 < nf) ? k + 1 : 0;
+                    const T ex = pg[(0 * MAXF + k1) * np + gi] - pg[(0 * MAXF + k) * np + gi];
+                    const T ey = pg[(1 * MAXF + k1) * np + gi] - pg[(1 * MAXF + k) * np + gi];
+                    const T inv = T(1) / sqrt(ex * ex + ey * ey);
+                    nhx = ey * inv;
+                    nhy = -ex * inv;
+                }
 #pragma unroll
                 for (int a = 1; a < FVLBM_Q; a++) {
-                    const T d = bc_delta<T, DEV>(kind, b, a, f[a], rho, ux, uy, feqs<T, DEV>(a, rho, ux, uy),
-                                                 nx * inv, ny * inv);
-                    gx[a - 1] += cx * d;
-                    gy[a - 1] += cy * d;
+                    const T d = bc_delta<T, DEV>(kind, b, a, f[a], rho, ux, uy, feqs<T, DEV>(a, rho, ux, uy), nhx, nhy);
+                    gx[a - 1] += cx[k] * d;
+                    gy[a - 1] += cy[k] * d;
                 }
             }
         }
@@ -305,6 +349,17 @@ __global__ void __launch_bounds__(TILE) stage_tile_kernel(DevView v, const S* __
     if (l >= nt) return;
     const int64_t gi = c0 + l;
     const InstParam& P = v.inst[v.grp[gi]];
+    uint32_t meta[MAXF];
+    T px[MAXF], py[MAXF];
+    int nf = 0;
+#pragma unroll
+    for (int k = 0; k < MAXF; k++) {
+        meta[k] = v.meta[k * np + gi];
+        px[k] = pg[(0 * MAXF + k) * np + gi];
+        py[k] = pg[(1 * MAXF + k) * np + gi];
+        nf += (meta[k] & 0xFF) != SK_NONE;
+    }
+    const T iarea = ((const T*)v.ia)[gi];
     T f[FVLBM_Q];
 #pragma unroll
     for (int a = 0; a < FVLBM_Q; a++) f[a] = fs[a * lmax + l];
@@ -315,15 +370,21 @@ __global__ void __launch_bounds__(TILE) stage_tile_kernel(DevView v, const S* __
     for (int a = 0; a < FVLBM_Q; a++) flux[a] = T(0);
 #pragma unroll
     for (int k = 0; k < MAXF; k++) {
-        const uint32_t meta = v.meta[k * np + gi];
-        const uint32_t kind = meta & 0xFF;
+        const uint32_t kind = meta[k] & 0xFF;
         if (kind == SK_NONE) continue;
-        const uint32_t mask = (meta >> 8) & 0xFF;
-        const T nx = nv[(0 * MAXF + k) * np + gi], ny = nv[(1 * MAXF + k) * np + gi];
-        const T rx = rv[(0 * MAXF + k) * np + gi], ry = rv[(1 * MAXF + k) * np + gi];
+        const uint32_t mask = (meta[k] >> 8) & 0xFF;
+        const int k1 = (k + 1 < nf) ? k + 1 : 0;
+        T qx = px[0], qy = py[0];
+#pragma unroll
+        for (int q = 1; q < MAXF; q++)
+            if (q == k1) { qx = px[q]; qy = py[q]; }
+        const T ex = qx - px[k], ey = qy - py[k];          // edge vector
+        const T nx = ey * iarea, ny = -ex * iarea;        // (dy, -dx) / A
+        const T rx = T(0.5) * (px[k] + qx), ry = T(0.5) * (py[k] + qy);   // midpoint - centroid
         if (kind == SK_INTERIOR) {
             const int lj = (int)v.lnbr[k * np + gi];
-            const T sx = rn[(0 * MAXF + k) * np + gi], sy = rn[(1 * MAXF + k) * np + gi];
+            // midpoint relative to the neighbour (its image across a periodic face)
+            const T sx = rx - dg[(0 * MAXF + k) * np + gi], sy = ry - dg[(1 * MAXF + k) * np + gi];
 #pragma unroll
             for (int a = 1; a < FVLBM_Q; a++) {
                 const T en = T(EXA(a)) * nx + T(EYA(a)) * ny;
@@ -335,8 +396,8 @@ __global__ void __launch_bounds__(TILE) stage_tile_kernel(DevView v, const S* __
                 flux[a] += en * (DEV ? face - f[a] : face);
             }
         } else {
-            const BcParam& b = v.bc[meta >> 16];
-            const T inv = T(1) / sqrt(nx * nx + ny * ny);
+            const BcParam& b = v.bc[meta[k] >> 16];
+            const T inv = T(1) / sqrt(ex * ex + ey * ey);
 #pragma unroll
             for (int a = 1; a < FVLBM_Q; a++) {
                 const bool out = (mask >> (a - 1)) & 1u;
@@ -347,7 +408,7 @@ __global__ void __launch_bounds__(TILE) stage_tile_kernel(DevView v, const S* __
                     face = f[a] + gxs[(a - 1) * gmax + l] * rx + gys[(a - 1) * gmax + l] * ry;
                 } else {
                     const T d = bc_delta<T, DEV>(kind, b, a, f[a], rho, ux, uy, feqs<T, DEV>(a, rho, ux, uy),
-                                                 nx * inv, ny * inv);
+                                                 ey * inv, -ex * inv);
                     face = kind == SK_SYMMETRY ? f[a] + T(0.5) * d : f[a] + d;
                 }
                 const T en = T(EXA(a)) * nx + T(EYA(a)) * ny;
@@ -378,7 +439,6 @@ __global__ void __launch_bounds__(TILE) stage_tile_kernel(DevView v, const S* __
     }
     if (bad) *v.flag = 1;
 }
-
 
 static inline unsigned grid_of(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 

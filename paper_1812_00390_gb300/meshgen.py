@@ -425,3 +425,125 @@ def bricks(nx: int = 8, ny: int = 6, U: float = 0.1, lx: float = 1.0, ly: float 
     be, bt = _rect_boundary(nx, ny, vid, (0, 0, 1, 0))
     bcs = [BC(BC_WALL), BC(BC_WALL, u_w=(U, 0.0))]
     return _pack(xy, cells, be, bt, bcs, f"bricks{nx}x{ny}")
+
+
+def tandem_cylinders(gap_ratio: float = 3.0, D: float = 1.0, n_circ: int = 160,
+                     first: float = 0.0015, growth: float = 1.1, r_far: float = 30.0,
+                     grade: float = 0.12, u_inf: float = 0.05, rho_inf: float = 1.0,
+                     seed: int = 0) -> Mesh:
+    """Two cylinders of diameter D in tandem, centres (0, 0) and (gap_ratio*D, 0)
+    (the tandem arrangement of Sec. 3.4).  Each has an O-grid of quads (first
+    radial spacing first*D, geometric growth) as thick as the gap allows; the
+    rest of the disc of radius r_far*D around the midpoint is filled with
+    triangles whose size grows with the distance from the cylinders (rate
+    `grade`), from a Delaunay triangulation of graded jittered points.  Walls on
+    both cylinders, far-field inlet / outlet as in cylinder_hybrid."""
+    from scipy.spatial import Delaunay
+    rng = np.random.default_rng(seed)
+    R = 0.5 * D
+    L = gap_ratio * D
+    centers = [(0.0, 0.0), (L, 0.0)]
+    thick = min(0.35 * (L - D), 1.0 * D)
+    radii = [R]
+    dr = first * D
+    while radii[-1] - R < thick:
+        radii.append(radii[-1] + dr)
+        dr *= growth
+    radii[-1] = R + thick
+    n_rad = len(radii) - 1
+    Ro = radii[-1]
+    th = 2.0 * np.pi * np.arange(n_circ) / n_circ
+    xy = []
+    cells = []
+    be, bt = [], []
+    for (cx, cy) in centers:
+        off = len(xy)
+        for r in radii:
+            for t in th:
+                xy.append((cx + r * math.cos(t), cy + r * math.sin(t)))
+        vid = lambda k, j, off=off: off + k * n_circ + (j % n_circ)
+        for k in range(n_rad):
+            for j in range(n_circ):
+                cells.append((vid(k, j), vid(k + 1, j), vid(k + 1, j + 1), vid(k, j + 1)))
+        for j in range(n_circ):
+            be.append((vid(0, j + 1), vid(0, j))); bt.append(0)
+    n_og = len(xy)
+    outer_ids = [[c * (n_rad + 1) * n_circ + n_rad * n_circ + j for j in range(n_circ)] for c in range(2)]
+    s_o = 2.0 * np.pi * Ro / n_circ
+    xm = 0.5 * L
+    Rf = r_far * D
+
+    def size(p):
+        d = min(math.hypot(p[0] - cx, p[1] - cy) for cx, cy in centers) - Ro
+        return s_o + grade * max(d, 0.0)
+
+    # far-field ring
+    h_far = size((xm + Rf, 0.0))
+    n_far = max(16, int(round(2 * np.pi * Rf / h_far)))
+    far_ids = []
+    for j in range(n_far):
+        t = 2 * np.pi * j / n_far
+        far_ids.append(len(xy))
+        xy.append((xm + Rf * math.cos(t), Rf * math.sin(t)))
+    # graded interior points: level l has spacing s_o * 2^l where size() falls in it
+    pts = []
+    h = s_o
+    while h < 2 * Rf:
+        nx = int(math.ceil(2 * Rf / h))
+        xs = xm - Rf + (np.arange(nx) + 0.5) * h
+        ys = -Rf + (np.arange(nx) + 0.5) * h
+        X, Y = np.meshgrid(xs, ys)
+        P = np.stack([X.ravel(), Y.ravel()], 1)
+        P = P + rng.uniform(-0.2, 0.2, P.shape) * h
+        d = np.min(np.stack([np.hypot(P[:, 0] - cx, P[:, 1] - cy) for cx, cy in centers]), 0) - Ro
+        sz = s_o + grade * np.maximum(d, 0.0)
+        keep = (sz >= h) & (sz < 2 * h) & (d > 0.6 * sz) & (np.hypot(P[:, 0] - xm, P[:, 1]) < Rf - 0.6 * sz)
+        if h == s_o:
+            keep = (sz < 2 * h) & (d > 0.6 * sz) & (np.hypot(P[:, 0] - xm, P[:, 1]) < Rf - 0.6 * sz)
+        pts.append(P[keep])
+        h *= 2
+    base = len(xy)
+    xy = np.array(xy + [tuple(p) for p in np.concatenate(pts)], dtype=np.float64)
+    # triangulate O-grid outer rings, far ring and field points
+    tri_ids = np.array(sum(outer_ids, []) + far_ids + list(range(base, len(xy))))
+    tri = Delaunay(xy[tri_ids])
+    simp = tri_ids[tri.simplices]
+    cen = xy[simp].mean(1)
+    inside = np.zeros(len(simp), bool)
+    for cx, cy in centers:
+        inside |= np.hypot(cen[:, 0] - cx, cen[:, 1] - cy) < Ro
+    inside |= np.hypot(cen[:, 0] - xm, cen[:, 1]) > Rf
+    simp = simp[~inside]
+    # CCW
+    a, b, c = xy[simp[:, 0]], xy[simp[:, 1]], xy[simp[:, 2]]
+    cr = (b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (c[:, 0] - a[:, 0])
+    simp[cr < 0] = simp[cr < 0][:, [0, 2, 1]]
+    # every O-grid outer edge and far-field edge must be a triangle edge
+    edges = set()
+    for t3 in simp:
+        for k in range(3):
+            edges.add(tuple(sorted((int(t3[k]), int(t3[(k + 1) % 3])))))
+    for ring in outer_ids:
+        for j in range(n_circ):
+            if tuple(sorted((ring[j], ring[(j + 1) % n_circ]))) not in edges:
+                raise ValueError("triangulation missed an O-grid edge; change grade or n_circ")
+    for j in range(n_far):
+        e = (far_ids[j], far_ids[(j + 1) % n_far])
+        if tuple(sorted(e)) not in edges:
+            raise ValueError("triangulation missed a far-field edge")
+        xmid = 0.5 * (xy[e[0], 0] + xy[e[1], 0])
+        be.append(e); bt.append(1 if xmid < xm else 2)
+    cells += [tuple(int(v) for v in t3) for t3 in simp]
+    # drop field points that ended up unused (none expected)
+    used = np.zeros(len(xy), bool)
+    for cl in cells:
+        used[list(cl)] = True
+    remap = -np.ones(len(xy), np.int64)
+    remap[used] = np.arange(used.sum())
+    xy = xy[used]
+    cells = [tuple(int(remap[v]) for v in cl) for cl in cells]
+    be = [(int(remap[a_]), int(remap[b_])) for a_, b_ in be]
+    bcs = [BC(BC_WALL),
+           BC(BC_INLET, external=1, rho_inf=rho_inf, u_inf=(u_inf, 0.0)),
+           BC(BC_OUTLET, external=1, rho_inf=rho_inf, u_inf=(u_inf, 0.0))]
+    return _pack(xy, cells, be, bt, bcs, f"tandem{gap_ratio:.2f}_{len(cells)}")
