@@ -106,8 +106,8 @@ typedef struct fvlbm_params {
     double u0[2];      /* initial velocity */
     int32_t device;    /* CUDA device ordinal; equal for all instances */
     int32_t kernel;    /* stage kernel: 0 = automatic; 1 = two kernels per stage (face
-                          values through memory); 128, 256 or 512 = one fused kernel per
-                          stage with that many cells per tile; equal for all instances */
+                          values through memory); 64 or 128 = one fused kernel per stage
+                          with that many cells per tile; equal for all instances */
 } fvlbm_params;
 
 typedef struct fvlbm_mesh_info_s {

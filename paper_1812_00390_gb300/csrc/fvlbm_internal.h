@@ -88,12 +88,12 @@ struct DevView {
     int32_t n_inst;
     // geometry, [maxf][np] planes
     const uint32_t* meta;  // kind | outmask << 8 | bc << 16
-    // two-kernel stage only
-    const int32_t* nbr;
-    const int32_t* fid;
     const void* cg;        // T [2][maxf][np]   least-squares coefficients
     const void* rv;        // T [2][maxf][np]   face midpoint - centroid
     const void* nv;        // T [2][maxf][np]   (dy, -dx) / A
+    // two-kernel stage only
+    const int32_t* nbr;
+    const int32_t* fid;
     const double* area;    // [np]
     const int32_t* grp;    // [np] instance of each cell
     const InstParam* inst; // [n_inst]
@@ -119,15 +119,13 @@ struct DevView {
     int64_t n_tiles;
     int32_t lmax;            // most local cells (tile + halo) of any tile
     int32_t gmax;            // most cells with a gradient (tile + 1-ring) of any tile
+    int32_t r1max;           // largest 1-ring of any tile
     const int64_t* halo_ptr; // [n_tiles + 1] into halo
     const int32_t* halo;     // 1-ring then 2-ring cells of each tile (global ids)
     const int32_t* n_r1;     // [n_tiles] 1-ring size
     const uint16_t* lnbr;    // [maxf][np] tile-local index of the neighbour across each face
     const uint16_t* r1nbr;   // [halo entries][maxf] tile-local stencil of 1-ring cells
-    // compact geometry of the fused stage: everything else is derived in-kernel
-    const void* pg;          // T [2][maxf][np] start vertex of each face - centroid
-    const void* dg;          // T [2][maxf][np] least-squares stencil point - centroid
-    const void* ia;          // T [np] 1 / area
+    const void* rn;          // T [2][maxf][np] neighbour-side face midpoint - neighbour centroid
 };
 
 enum Strategy { STRATEGY_TWO_KERNEL = 0, STRATEGY_TILE = 1 };
@@ -141,9 +139,21 @@ int launch_stage(const DevView& v, int prec, void* stream, const void* fin, cons
 // Most kernels launched by one stage (two-kernel strategy).
 constexpr int STAGE_KERNELS = 2;
 inline int stage_kernels(const DevView& v) { return v.strategy == STRATEGY_TILE ? 1 : 2; }
-// Dynamic shared memory of the fused stage kernel for real type of `rsize` bytes.
+// Dynamic shared memory of the fused stage kernel: f of tile and halo,
+// gradients and macros of tile and 1-ring, the tile's geometry (meta, local
+// neighbour, 4 vectors per slot, instance) and the 1-ring's (meta, local
+// stencil, least-squares vector per slot), for real type of `rsize` bytes.
+inline size_t smem_round(size_t b) { return (b + 15) / 16 * 16; }
+inline size_t tile_smem_bytes_for(int tile, int maxf, int lmax, int gmax, int r1max, int rsize) {
+    const size_t R = (size_t)rsize, tl = (size_t)tile, mf = (size_t)maxf, r1 = (size_t)r1max;
+    size_t b = smem_round(R * FVLBM_Q * lmax) + 2 * smem_round(R * (FVLBM_Q - 1) * gmax) + smem_round(R * 3 * gmax);
+    b += 4 * smem_round(R * 2 * mf * tl) + smem_round(R * 2 * mf * r1);
+    b += smem_round(4 * mf * tl) + smem_round(4 * tl) + smem_round(4 * mf * r1);
+    b += smem_round(2 * mf * tl) + smem_round(2 * mf * r1);
+    return b;
+}
 inline size_t tile_smem_bytes(const DevView& v, size_t rsize) {
-    return rsize * ((size_t)FVLBM_Q * v.lmax + 2 * (FVLBM_Q - 1) * (size_t)v.gmax);
+    return tile_smem_bytes_for(v.tile, v.maxf, v.lmax, v.gmax, v.r1max, (int)rsize);
 }
 // One translation unit per state precision.
 int stage_fp64(const DevView& v, void* stream, const void* fin, const void* fbase, void* fout, double beta, int mode,

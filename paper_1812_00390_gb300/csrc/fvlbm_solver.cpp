@@ -78,7 +78,7 @@ size_t store_size(int prec) {
 struct TilePlan {
     int tile = 0;
     int64_t n_tiles = 0;
-    int32_t lmax = 0, gmax = 0;
+    int32_t lmax = 0, gmax = 0, r1max = 0;
     std::vector<int64_t> halo_ptr;
     std::vector<int32_t> halo;
     std::vector<int32_t> n_r1;
@@ -149,6 +149,7 @@ void make_tiles(const Mesh& M, int64_t np, int maxf, int tile, TilePlan& P) {
         P.n_r1[t] = n1;
         P.lmax = std::max(P.lmax, nl);
         P.gmax = std::max<int32_t>(P.gmax, (int32_t)(c1 - c0) + n1);
+        P.r1max = std::max<int32_t>(P.r1max, n1);
     }
     P.r1nbr.swap(r1nbr);
 }
@@ -161,14 +162,14 @@ struct Layout {
     TilePlan tp;
     size_t off_nbr, off_fid, off_meta, off_cg, off_rv, off_nv, off_area, off_grp, off_inst, off_bc,
         off_fa, off_fb, off_rprev, off_fv, off_rho, off_ux, off_uy, off_uold, off_part, off_red, off_conv,
-        off_chunk, off_flag, off_hptr, off_halo, off_nr1, off_lnbr, off_r1nbr, off_pg, off_dg, off_ia, total;
+        off_chunk, off_flag, off_hptr, off_halo, off_nr1, off_lnbr, off_r1nbr, off_rn, total;
 };
 
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 constexpr int64_t PLANE_ALIGN = 512;   // planes hold whole tiles of the largest tile size
 
-// kernel: 0 automatic (fused tile 256, except FP64: two kernels, which spend
-// fewer FP64 operations), 1 two-kernel, 128/256/512 fused with that tile size.
+// kernel: 0 automatic (fused tile 128, except FP64: two kernels, which spend
+// fewer FP64 operations), 1 two-kernel, 64/128 fused with that tile size.
 int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L) {
     L = Layout{};
     L.np = (M.n_cell + PLANE_ALIGN - 1) / PLANE_ALIGN * PLANE_ALIGN;
@@ -177,12 +178,12 @@ int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L) {
     L.n_chunk = 0;
     for (int k = 0; k < M.n_inst; k++) L.n_chunk += (M.inst_begin[k + 1] - M.inst_begin[k] + CHUNK - 1) / CHUNK;
     const size_t R = real_size(prec), S = store_size(prec);
-    if (kernel != 0 && kernel != 1 && kernel != 128 && kernel != 256 && kernel != 512)
-        return fail(FVLBM_ERR_ARG, "params.kernel = %d: use 0, 1, 128, 256 or 512", kernel);
+    if (kernel != 0 && kernel != 1 && kernel != 64 && kernel != 128)
+        return fail(FVLBM_ERR_ARG, "params.kernel = %d: use 0, 1, 64 or 128", kernel);
     L.strategy = (kernel == 1 || (kernel == 0 && prec == FVLBM_FP64)) ? STRATEGY_TWO_KERNEL : STRATEGY_TILE;
     if (L.strategy == STRATEGY_TILE) {
-        make_tiles(M, L.np, L.maxf, kernel == 0 ? 256 : kernel, L.tp);
-        const size_t smem = R * ((size_t)FVLBM_Q * L.tp.lmax + 2 * (FVLBM_Q - 1) * (size_t)L.tp.gmax);
+        make_tiles(M, L.np, L.maxf, kernel == 0 ? 128 : kernel, L.tp);
+        const size_t smem = tile_smem_bytes_for(L.tp.tile, L.maxf, L.tp.lmax, L.tp.gmax, L.tp.r1max, (int)R);
         if (smem > SMEM_LIMIT || L.tp.lmax >= 0xFFFF) {
             if (kernel != 0)
                 return fail(FVLBM_ERR_UNSUPPORTED, "fused stage needs %zu B of shared memory per tile (limit %zu)",
@@ -206,17 +207,15 @@ int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L) {
     L.off_bc = take(sizeof(BcParam) * std::max<size_t>(1, M.bcs.size()));
     L.off_nbr = take(two ? 4 * slots : 0);
     L.off_fid = take(two ? 4 * slots : 0);
-    L.off_cg = take(two ? R * slots * 2 : 0);
-    L.off_rv = take(two ? R * slots * 2 : 0);
-    L.off_nv = take(two ? R * slots * 2 : 0);
+    L.off_cg = take(R * slots * 2);
+    L.off_rv = take(R * slots * 2);
+    L.off_nv = take(R * slots * 2);
     L.off_hptr = take(tiled ? 8 * (size_t)(L.tp.n_tiles + 1) : 0);
     L.off_halo = take(tiled ? 4 * L.tp.halo.size() : 0);
     L.off_nr1 = take(tiled ? 4 * (size_t)L.tp.n_tiles : 0);
     L.off_lnbr = take(tiled ? 2 * slots : 0);
     L.off_r1nbr = take(tiled ? 2 * L.tp.r1nbr.size() : 0);
-    L.off_pg = take(tiled ? R * slots * 2 : 0);
-    L.off_dg = take(tiled ? R * slots * 2 : 0);
-    L.off_ia = take(tiled ? R * plane : 0);
+    L.off_rn = take(tiled ? R * slots * 2 : 0);
     L.off_fa = take(S * plane * FVLBM_Q);   // everything before this is uploaded once
     L.off_fb = (scheme == FVLBM_RK2 || scheme == FVLBM_RK4) ? take(S * plane * FVLBM_Q) : 0;
     L.off_rprev = scheme == FVLBM_AB2 ? take(R * plane * FVLBM_Q) : 0;
@@ -275,12 +274,10 @@ void pack_geometry(const Mesh& M, const Layout& L, std::vector<unsigned char>& h
     int32_t* grp = (int32_t*)(H + L.off_grp);
     int32_t* nbr = two ? (int32_t*)(H + L.off_nbr) : nullptr;
     int32_t* fid = two ? (int32_t*)(H + L.off_fid) : nullptr;
-    T* cg = two ? (T*)(H + L.off_cg) : nullptr;
-    T* rv = two ? (T*)(H + L.off_rv) : nullptr;
-    T* nv = two ? (T*)(H + L.off_nv) : nullptr;
-    T* pg = two ? nullptr : (T*)(H + L.off_pg);
-    T* dg = two ? nullptr : (T*)(H + L.off_dg);
-    T* ia = two ? nullptr : (T*)(H + L.off_ia);
+    T* cg = (T*)(H + L.off_cg);
+    T* rv = (T*)(H + L.off_rv);
+    T* nv = (T*)(H + L.off_nv);
+    T* rn = two ? nullptr : (T*)(H + L.off_rn);
     for (int64_t x = 0; x < (int64_t)maxf * np; x++) {
         meta[x] = SK_NONE;
         if (two) nbr[x] = fid[x] = -1;
@@ -292,7 +289,6 @@ void pack_geometry(const Mesh& M, const Layout& L, std::vector<unsigned char>& h
         while (g + 1 < M.n_inst && c >= M.inst_begin[g + 1]) g++;
         grp[i] = g;
         area[i] = M.area[c];
-        if (ia) ia[i] = (T)(1.0 / M.area[c]);
         for (int k = 0; k < M.nf[c]; k++) {
             const Slot& S = M.slots[(size_t)c * MAXP + k];
             const int64_t x = (int64_t)k * np + i;
@@ -309,17 +305,18 @@ void pack_geometry(const Mesh& M, const Layout& L, std::vector<unsigned char>& h
                 } else {
                     fid[x] = (int32_t)next++;
                 }
-                cg[(0 * maxf + k) * np + i] = (T)S.cgx;
-                cg[(1 * maxf + k) * np + i] = (T)S.cgy;
-                rv[(0 * maxf + k) * np + i] = (T)(S.px - M.cx[c]);
-                rv[(1 * maxf + k) * np + i] = (T)(S.py - M.cy[c]);
-                nv[(0 * maxf + k) * np + i] = (T)(S.nx / M.area[c]);
-                nv[(1 * maxf + k) * np + i] = (T)(S.ny / M.area[c]);
-            } else {
-                pg[(0 * maxf + k) * np + i] = (T)(S.vx - M.cx[c]);
-                pg[(1 * maxf + k) * np + i] = (T)(S.vy - M.cy[c]);
-                dg[(0 * maxf + k) * np + i] = (T)S.sdx;
-                dg[(1 * maxf + k) * np + i] = (T)S.sdy;
+            }
+            cg[(0 * maxf + k) * np + i] = (T)S.cgx;
+            cg[(1 * maxf + k) * np + i] = (T)S.cgy;
+            rv[(0 * maxf + k) * np + i] = (T)(S.px - M.cx[c]);
+            rv[(1 * maxf + k) * np + i] = (T)(S.py - M.cy[c]);
+            nv[(0 * maxf + k) * np + i] = (T)(S.nx / M.area[c]);
+            nv[(1 * maxf + k) * np + i] = (T)(S.ny / M.area[c]);
+            if (rn && S.kind == SK_INTERIOR) {
+                // the neighbour's own reconstruction vector to this face
+                const Slot& Q = M.slots[(size_t)S.nb * MAXP + S.nb_slot];
+                rn[(0 * maxf + k) * np + i] = (T)(Q.px - M.cx[S.nb]);
+                rn[(1 * maxf + k) * np + i] = (T)(Q.py - M.cy[S.nb]);
             }
         }
     }
@@ -515,14 +512,13 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
         v.n_tiles = L.tp.n_tiles;
         v.lmax = L.tp.lmax;
         v.gmax = L.tp.gmax;
+        v.r1max = L.tp.r1max;
         v.halo_ptr = (const int64_t*)(base + L.off_hptr);
         v.halo = (const int32_t*)(base + L.off_halo);
         v.n_r1 = (const int32_t*)(base + L.off_nr1);
         v.lnbr = (const uint16_t*)(base + L.off_lnbr);
         v.r1nbr = (const uint16_t*)(base + L.off_r1nbr);
-        v.pg = base + L.off_pg;
-        v.dg = base + L.off_dg;
-        v.ia = base + L.off_ia;
+        v.rn = base + L.off_rn;
     }
 
     // Step 0 and the first residual snapshot
