@@ -106,8 +106,8 @@ typedef struct fvlbm_params {
     double u0[2];      /* initial velocity */
     int32_t device;    /* CUDA device ordinal; equal for all instances */
     int32_t kernel;    /* stage kernel: 0 = automatic; 1 = two kernels per stage (face
-                          values through memory); 64 or 128 = one fused kernel per stage
-                          with that many cells per tile; equal for all instances */
+                          values through memory); 128, 256 or 512 = one fused kernel per
+                          stage with that many cells per tile; equal for all instances */
 } fvlbm_params;
 
 typedef struct fvlbm_mesh_info_s {
@@ -268,6 +268,69 @@ int fvlbm_profile(fvlbm_solver* s, int64_t n, double* avg_ms, int32_t max_kinds,
 int fvlbm_launches_per_step(const fvlbm_solver* s, int64_t* launches);
 
 void fvlbm_solver_destroy(fvlbm_solver* s);
+
+/*
+ * Continuous-batching solve server (one GPU).  Requests are queued in arrival
+ * order; every fvlbm_server_poll round
+ *   1. advances every active request by check_interval time steps (the
+ *      residual interval of Sec. 3.2), each request on one of n_streams
+ *      streams so that the kernels of different requests overlap;
+ *   2. admits queued requests, first fit in arrival order, while fewer than
+ *      max_active are active and the device arena (arena_bytes, allocated once
+ *      at creation) has a free block for the request's workspace;
+ *   3. checks the velocity residual of the requests advanced in step 1 and
+ *      retires those with e <= residual_tol or max_steps steps done: rho and u
+ *      are copied to host memory and the workspace returns to the arena.
+ * A request is an ordinary solver on its own workspace: its result does not
+ * depend on the other requests.
+ */
+typedef struct fvlbm_server fvlbm_server;
+
+typedef struct fvlbm_server_config {
+    int32_t device;
+    int32_t n_streams;      /* 1..64 */
+    size_t arena_bytes;     /* device memory budget for request workspaces */
+    int32_t max_active;     /* most requests on the device at once */
+    int32_t check_interval; /* time steps between residual checks (the paper uses 1000) */
+    double residual_tol;    /* converged when the residual is <= this (e.g. 1e-8) */
+    int64_t max_steps;      /* step cap per request */
+} fvlbm_server_config;
+
+typedef enum fvlbm_request_state {
+    FVLBM_REQ_QUEUED = 0, FVLBM_REQ_ACTIVE = 1, FVLBM_REQ_DONE = 2, FVLBM_REQ_FAILED = 3
+} fvlbm_request_state;
+
+typedef struct fvlbm_request_info {
+    int32_t state;          /* fvlbm_request_state */
+    int32_t status;         /* fvlbm_status of a failed request */
+    int64_t steps;          /* time steps done */
+    int64_t n_cell;
+    double residual;        /* last residual */
+    double t_submit, t_admit, t_done;  /* seconds since the server was created */
+    size_t workspace_bytes;
+} fvlbm_request_info;
+
+typedef struct fvlbm_server_stats_s {
+    int32_t queued, active;
+    size_t arena_free, arena_free_largest;
+    int64_t cell_steps;     /* cell updates done so far */
+    double t_now;           /* seconds since creation */
+} fvlbm_server_stats_t;
+
+/* Create (allocates the arena and the streams).  Errors: ARG, OOM, CUDA, UNSUPPORTED. */
+int fvlbm_server_create(const fvlbm_server_config* cfg, fvlbm_server** out);
+/* Queue a request.  mesh must stay valid until the request is done; params
+ * host [n_params] as for fvlbm_init, device equal to the server's.  id: host,
+ * written.  Errors: ARG, OOM (workspace larger than the whole arena). */
+int fvlbm_server_submit(fvlbm_server* s, const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t n_params,
+                        int64_t* id);
+/* One scheduling round (see above); n_completed: host, written (may be NULL). */
+int fvlbm_server_poll(fvlbm_server* s, int32_t* n_completed);
+/* State of a request; rho [n_cell] and u [n_cell][2] (host, may be NULL) are
+ * written once it is done, in the caller's cell order. */
+int fvlbm_server_request(fvlbm_server* s, int64_t id, fvlbm_request_info* info, double* rho, double* u);
+int fvlbm_server_stats(const fvlbm_server* s, fvlbm_server_stats_t* stats);
+void fvlbm_server_destroy(fvlbm_server* s);
 
 /* Message of the last failure on this thread ("" if none). */
 const char* fvlbm_last_error(void);

@@ -143,17 +143,13 @@ inline int stage_kernels(const DevView& v) { return v.strategy == STRATEGY_TILE 
 // gradients and macros of tile and 1-ring, the tile's geometry (meta, local
 // neighbour, 4 vectors per slot, instance) and the 1-ring's (meta, local
 // stencil, least-squares vector per slot), for real type of `rsize` bytes.
-inline size_t smem_round(size_t b) { return (b + 15) / 16 * 16; }
-inline size_t tile_smem_bytes_for(int tile, int maxf, int lmax, int gmax, int r1max, int rsize) {
-    const size_t R = (size_t)rsize, tl = (size_t)tile, mf = (size_t)maxf, r1 = (size_t)r1max;
-    size_t b = smem_round(R * FVLBM_Q * lmax) + 2 * smem_round(R * (FVLBM_Q - 1) * gmax) + smem_round(R * 3 * gmax);
-    b += 4 * smem_round(R * 2 * mf * tl) + smem_round(R * 2 * mf * r1);
-    b += smem_round(4 * mf * tl) + smem_round(4 * tl) + smem_round(4 * mf * r1);
-    b += smem_round(2 * mf * tl) + smem_round(2 * mf * r1);
-    return b;
+// Dynamic shared memory of the fused stage kernel: f of tile and halo, and
+// the gradients of tile and 1-ring cells, for real type of `rsize` bytes.
+inline size_t tile_smem_bytes_for(int lmax, int gmax, int rsize) {
+    return (size_t)rsize * ((size_t)FVLBM_Q * lmax + 2 * (FVLBM_Q - 1) * (size_t)gmax);
 }
 inline size_t tile_smem_bytes(const DevView& v, size_t rsize) {
-    return tile_smem_bytes_for(v.tile, v.maxf, v.lmax, v.gmax, v.r1max, (int)rsize);
+    return tile_smem_bytes_for(v.lmax, v.gmax, (int)rsize);
 }
 // One translation unit per state precision.
 int stage_fp64(const DevView& v, void* stream, const void* fin, const void* fbase, void* fout, double beta, int mode,

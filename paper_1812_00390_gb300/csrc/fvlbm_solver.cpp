@@ -168,8 +168,8 @@ struct Layout {
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 constexpr int64_t PLANE_ALIGN = 512;   // planes hold whole tiles of the largest tile size
 
-// kernel: 0 automatic (fused tile 128, except FP64: two kernels, which spend
-// fewer FP64 operations), 1 two-kernel, 64/128 fused with that tile size.
+// kernel: 0 automatic (fused tile 256, except FP64: two kernels, which spend
+// fewer FP64 operations), 1 two-kernel, 128/256/512 fused with that tile size.
 int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L) {
     L = Layout{};
     L.np = (M.n_cell + PLANE_ALIGN - 1) / PLANE_ALIGN * PLANE_ALIGN;
@@ -178,12 +178,12 @@ int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L) {
     L.n_chunk = 0;
     for (int k = 0; k < M.n_inst; k++) L.n_chunk += (M.inst_begin[k + 1] - M.inst_begin[k] + CHUNK - 1) / CHUNK;
     const size_t R = real_size(prec), S = store_size(prec);
-    if (kernel != 0 && kernel != 1 && kernel != 64 && kernel != 128)
-        return fail(FVLBM_ERR_ARG, "params.kernel = %d: use 0, 1, 64 or 128", kernel);
+    if (kernel != 0 && kernel != 1 && kernel != 128 && kernel != 256 && kernel != 512)
+        return fail(FVLBM_ERR_ARG, "params.kernel = %d: use 0, 1, 128, 256 or 512", kernel);
     L.strategy = (kernel == 1 || (kernel == 0 && prec == FVLBM_FP64)) ? STRATEGY_TWO_KERNEL : STRATEGY_TILE;
     if (L.strategy == STRATEGY_TILE) {
-        make_tiles(M, L.np, L.maxf, kernel == 0 ? 128 : kernel, L.tp);
-        const size_t smem = tile_smem_bytes_for(L.tp.tile, L.maxf, L.tp.lmax, L.tp.gmax, L.tp.r1max, (int)R);
+        make_tiles(M, L.np, L.maxf, kernel == 0 ? 256 : kernel, L.tp);
+        const size_t smem = tile_smem_bytes_for(L.tp.lmax, L.tp.gmax, (int)R);
         if (smem > SMEM_LIMIT || L.tp.lmax >= 0xFFFF) {
             if (kernel != 0)
                 return fail(FVLBM_ERR_UNSUPPORTED, "fused stage needs %zu B of shared memory per tile (limit %zu)",

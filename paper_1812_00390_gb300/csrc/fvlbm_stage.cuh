@@ -214,50 +214,23 @@ __global__ void __launch_bounds__(256) update_kernel(DevView v, const S* __restr
     if (bad) *v.flag = 1;
 }
 
-// Fused stage: one CTA of 8*TILE threads per tile of TILE consecutive cells
-// (Hilbert order).  Work is spread over (cell, direction) items -- lanes over
-// cells, warps over directions -- so that each thread holds little state and
-// the SM keeps many warps in flight.
-//   phase 1  f of the tile, its 1-ring and its 2-ring, the tile's geometry and
-//            the 1-ring's least-squares data into shared memory; then rho, u
-//            of tile and 1-ring cells (Sec. 2.1)
-//   phase 2  gradient of f_a (Eq. leastsquare) for every tile and 1-ring cell
-//            and direction a = 1..8 (boundary stencil values of Sec. 2.4.1)
-//   phase 3  for every tile cell and direction: face values from the upwind
-//            side (Eq. lslrflux, Sec. 2.4.2) -- the cell's own gradient or the
-//            neighbour's -- flux sum, collision and time update (Eq. rhs,
-//            Sec. 2.3), written to global memory
+// Fused stage: one CTA per tile of TILE consecutive cells (Hilbert order).
+//   phase 1  f of the tile, its 1-ring and its 2-ring into shared memory
+//   phase 2  gradients (Eq. leastsquare) of the tile and 1-ring cells, kept in
+//            shared memory
+//   phase 3  per tile cell: face values (Eq. lslrflux / Sec. 2.4.2) from the
+//            upwind side -- its own gradient, or the neighbour's from shared
+//            memory -- flux sum, collision and time update (Eq. rhs, Sec. 2.3)
 // Each face value is evaluated by both cells of the face from the same data,
-// so no face value goes through global memory; there are no atomics.
-template <typename T>
-__device__ __forceinline__ T* smem_take(unsigned char*& p, size_t n) {
-    T* r = (T*)p;
-    p += (n * sizeof(T) + 15) / 16 * 16;
-    return r;
-}
-
+// so no face-value array goes through memory.
 template <typename T, typename S, int MAXF, bool DEV, int TILE>
-__global__ void __launch_bounds__(8 * TILE) stage_tile_kernel(DevView v, const S* __restrict__ fin,
-                                                              const S* fbase, S* fout, T beta, int mode) {
-    constexpr int NT = 8 * TILE;
+__global__ void __launch_bounds__(TILE) stage_tile_kernel(DevView v, const S* __restrict__ fin,
+                                                          const S* fbase, S* fout, T beta, int mode) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lmax = v.lmax, gmax = v.gmax, r1max = v.r1max;
-    unsigned char* sp = smem_raw;
-    T* fs = smem_take<T>(sp, (size_t)FVLBM_Q * lmax);
-    T* gxs = smem_take<T>(sp, (size_t)(FVLBM_Q - 1) * gmax);
-    T* gys = smem_take<T>(sp, (size_t)(FVLBM_Q - 1) * gmax);
-    T* mac = smem_take<T>(sp, (size_t)3 * gmax);
-    T* tcg = smem_take<T>(sp, (size_t)2 * MAXF * TILE);
-    T* trv = smem_take<T>(sp, (size_t)2 * MAXF * TILE);
-    T* trn = smem_take<T>(sp, (size_t)2 * MAXF * TILE);
-    T* tnv = smem_take<T>(sp, (size_t)2 * MAXF * TILE);
-    T* rcg = smem_take<T>(sp, (size_t)2 * MAXF * r1max);
-    uint32_t* tmeta = smem_take<uint32_t>(sp, (size_t)MAXF * TILE);
-    int32_t* tgrp = smem_take<int32_t>(sp, (size_t)TILE);
-    uint32_t* rmeta = smem_take<uint32_t>(sp, (size_t)MAXF * r1max);
-    uint16_t* tlnbr = smem_take<uint16_t>(sp, (size_t)MAXF * TILE);
-    uint16_t* rlnbr = smem_take<uint16_t>(sp, (size_t)MAXF * r1max);
-
+    const int lmax = v.lmax, gmax = v.gmax;
+    T* fs = (T*)smem_raw;            // [9][lmax]
+    T* gxs = fs + FVLBM_Q * lmax;    // [8][gmax]
+    T* gys = gxs + (FVLBM_Q - 1) * gmax;
     const int64_t np = v.np;
     const int64_t t = blockIdx.x;
     const int64_t c0 = t * TILE;
@@ -265,168 +238,139 @@ __global__ void __launch_bounds__(8 * TILE) stage_tile_kernel(DevView v, const S
     const int64_t h0 = v.halo_ptr[t];
     const int nh = (int)(v.halo_ptr[t + 1] - h0);
     const int n1 = v.n_r1[t];
-    const int ng = nt + n1;
-    const int tid = threadIdx.x;
+    const int nl = nt + nh;
     const T* cg = (const T*)v.cg;
     const T* rv = (const T*)v.rv;
     const T* rn = (const T*)v.rn;
     const T* nv = (const T*)v.nv;
 
-    // ---- phase 1: stage f and geometry (planes are padded to whole tiles)
-    for (int q = tid; q < FVLBM_Q * TILE; q += NT) {
-        const int a = q / TILE, l = q - a * TILE;
-        if (l < nt) {
-            const int64_t gi = c0 + l;
-            const InstParam& P = v.inst[v.grp[gi]];
-            fs[a * lmax + l] = Store<S>::ld(fin, a * np + gi, P.inv_scale[a], P.off[a]);
-        }
-    }
-    for (int q = tid; q < FVLBM_Q * nh; q += NT) {
-        const int a = q / nh, h = q - a * nh;
-        const int64_t gi = v.halo[h0 + h];
+    // phase 1
+    for (int l = threadIdx.x; l < nl; l += TILE) {
+        const int64_t gi = l < nt ? c0 + l : (int64_t)v.halo[h0 + l - nt];
         const InstParam& P = v.inst[v.grp[gi]];
-        fs[a * lmax + nt + h] = Store<S>::ld(fin, a * np + gi, P.inv_scale[a], P.off[a]);
-    }
-    for (int q = tid; q < MAXF * TILE; q += NT) {
-        const int k = q / TILE, l = q - k * TILE;
-        const int64_t gi = c0 + l;
-        tmeta[q] = v.meta[k * np + gi];
-        tlnbr[q] = v.lnbr[k * np + gi];
 #pragma unroll
-        for (int c = 0; c < 2; c++) {
-            const int64_t gq = (int64_t)(c * MAXF + k) * np + gi;
-            const int sq = (c * MAXF + k) * TILE + l;
-            tcg[sq] = cg[gq];
-            trv[sq] = rv[gq];
-            trn[sq] = rn[gq];
-            tnv[sq] = nv[gq];
-        }
-    }
-    for (int q = tid; q < TILE; q += NT) tgrp[q] = v.grp[c0 + q];
-    for (int q = tid; q < MAXF * n1; q += NT) {
-        const int k = q / n1, j = q - k * n1;
-        const int64_t gi = v.halo[h0 + j];
-        rmeta[k * r1max + j] = v.meta[k * np + gi];
-        rlnbr[k * r1max + j] = v.r1nbr[(h0 + j) * MAXF + k];
-        rcg[(0 * MAXF + k) * r1max + j] = cg[(int64_t)(0 * MAXF + k) * np + gi];
-        rcg[(1 * MAXF + k) * r1max + j] = cg[(int64_t)(1 * MAXF + k) * np + gi];
+        for (int a = 0; a < FVLBM_Q; a++) fs[a * lmax + l] = Store<S>::ld(fin, a * np + gi, P.inv_scale[a], P.off[a]);
     }
     __syncthreads();
-    for (int l = tid; l < ng; l += NT) {
+
+    // phase 2
+    for (int l = threadIdx.x; l < nt + n1; l += TILE) {
+        const bool own = l < nt;
+        const int64_t gi = own ? c0 + l : (int64_t)v.halo[h0 + l - nt];
         T f[FVLBM_Q];
 #pragma unroll
         for (int a = 0; a < FVLBM_Q; a++) f[a] = fs[a * lmax + l];
-        T r, ux, uy;
-        moments<T, DEV>(f, r, ux, uy);
-        mac[l] = r;
-        mac[gmax + l] = ux;
-        mac[2 * gmax + l] = uy;
-    }
-    __syncthreads();
-
-    // ---- phase 2: gradients of f_1..f_8 for tile and 1-ring cells
-    for (int q = tid; q < (FVLBM_Q - 1) * ng; q += NT) {
-        const int a = 1 + q / ng, l = q - (a - 1) * ng;
-        const bool own = l < nt;
-        const T fa = fs[a * lmax + l];
-        const T r = mac[l], ux = mac[gmax + l], uy = mac[2 * gmax + l];
-        T gx = 0, gy = 0;
+        T rho, ux, uy;
+        moments<T, DEV>(f, rho, ux, uy);
+        T gx[FVLBM_Q - 1], gy[FVLBM_Q - 1];
+#pragma unroll
+        for (int a = 0; a < FVLBM_Q - 1; a++) gx[a] = gy[a] = T(0);
 #pragma unroll
         for (int k = 0; k < MAXF; k++) {
-            const uint32_t meta = own ? tmeta[k * TILE + l] : rmeta[k * r1max + (l - nt)];
+            const uint32_t meta = v.meta[k * np + gi];
             const uint32_t kind = meta & 0xFF;
             if (kind == SK_NONE) continue;
-            const T cx = own ? tcg[(0 * MAXF + k) * TILE + l] : rcg[(0 * MAXF + k) * r1max + (l - nt)];
-            const T cy = own ? tcg[(1 * MAXF + k) * TILE + l] : rcg[(1 * MAXF + k) * r1max + (l - nt)];
-            T d;
+            const T cx = cg[(0 * MAXF + k) * np + gi], cy = cg[(1 * MAXF + k) * np + gi];
             if (kind == SK_INTERIOR) {
-                const int lj = own ? (int)tlnbr[k * TILE + l] : (int)rlnbr[k * r1max + (l - nt)];
-                d = fs[a * lmax + lj] - fa;
-            } else {
-                T nhx = 0, nhy = 0;
-                if (kind == SK_SYMMETRY) {
-                    T nx, ny;
-                    if (own) {
-                        nx = tnv[(0 * MAXF + k) * TILE + l];
-                        ny = tnv[(1 * MAXF + k) * TILE + l];
-                    } else {
-                        const int64_t gi = v.halo[h0 + (l - nt)];
-                        nx = nv[(int64_t)(0 * MAXF + k) * np + gi];
-                        ny = nv[(int64_t)(1 * MAXF + k) * np + gi];
-                    }
-                    const T inv = T(1) / sqrt(nx * nx + ny * ny);
-                    nhx = nx * inv;
-                    nhy = ny * inv;
+                const int lj = own ? (int)v.lnbr[k * np + gi] : (int)v.r1nbr[(h0 + l - nt) * MAXF + k];
+#pragma unroll
+                for (int a = 1; a < FVLBM_Q; a++) {
+                    const T d = fs[a * lmax + lj] - f[a];
+                    gx[a - 1] += cx * d;
+                    gy[a - 1] += cy * d;
                 }
-                d = bc_delta<T, DEV>(kind, v.bc[meta >> 16], a, fa, r, ux, uy, feqs<T, DEV>(a, r, ux, uy), nhx, nhy);
+            } else {
+                const BcParam& b = v.bc[meta >> 16];
+                const T nx = nv[(0 * MAXF + k) * np + gi], ny = nv[(1 * MAXF + k) * np + gi];
+                const T inv = T(1) / sqrt(nx * nx + ny * ny);
+#pragma unroll
+                for (int a = 1; a < FVLBM_Q; a++) {
+                    const T d = bc_delta<T, DEV>(kind, b, a, f[a], rho, ux, uy, feqs<T, DEV>(a, rho, ux, uy),
+                                                 nx * inv, ny * inv);
+                    gx[a - 1] += cx * d;
+                    gy[a - 1] += cy * d;
+                }
             }
-            gx += cx * d;
-            gy += cy * d;
         }
-        gxs[(a - 1) * gmax + l] = gx;
-        gys[(a - 1) * gmax + l] = gy;
+#pragma unroll
+        for (int a = 0; a < FVLBM_Q - 1; a++) {
+            gxs[a * gmax + l] = gx[a];
+            gys[a * gmax + l] = gy[a];
+        }
     }
     __syncthreads();
 
-    // ---- phase 3: flux, collision and update of every tile cell and direction
-    T* rp = (T*)v.rprev;
-    bool bad = false;
-    for (int q = tid; q < FVLBM_Q * nt; q += NT) {
-        const int a = q / nt, l = q - a * nt;
-        const int64_t gi = c0 + l;
-        const T fa = fs[a * lmax + l];
-        const T r = mac[l], ux = mac[gmax + l], uy = mac[2 * gmax + l];
-        const T ea_x = T(EXA(a)), ea_y = T(EYA(a));
-        T flux = 0;
-        if (a > 0) {
-            const T gxo = gxs[(a - 1) * gmax + l], gyo = gys[(a - 1) * gmax + l];
+    // phase 3
+    const int l = threadIdx.x;
+    if (l >= nt) return;
+    const int64_t gi = c0 + l;
+    const InstParam& P = v.inst[v.grp[gi]];
+    T f[FVLBM_Q];
 #pragma unroll
-            for (int k = 0; k < MAXF; k++) {
-                const uint32_t meta = tmeta[k * TILE + l];
-                const uint32_t kind = meta & 0xFF;
-                if (kind == SK_NONE) continue;
-                const int sq = k * TILE + l;
-                const T nx = tnv[sq], ny = tnv[MAXF * TILE + sq];
-                const T rx = trv[sq], ry = trv[MAXF * TILE + sq];
-                const bool out = (meta >> (8 + a - 1)) & 1u;
+    for (int a = 0; a < FVLBM_Q; a++) f[a] = fs[a * lmax + l];
+    T rho, ux, uy;
+    moments<T, DEV>(f, rho, ux, uy);
+    T flux[FVLBM_Q];
+#pragma unroll
+    for (int a = 0; a < FVLBM_Q; a++) flux[a] = T(0);
+#pragma unroll
+    for (int k = 0; k < MAXF; k++) {
+        const uint32_t meta = v.meta[k * np + gi];
+        const uint32_t kind = meta & 0xFF;
+        if (kind == SK_NONE) continue;
+        const uint32_t mask = (meta >> 8) & 0xFF;
+        const T nx = nv[(0 * MAXF + k) * np + gi], ny = nv[(1 * MAXF + k) * np + gi];
+        const T rx = rv[(0 * MAXF + k) * np + gi], ry = rv[(1 * MAXF + k) * np + gi];
+        if (kind == SK_INTERIOR) {
+            const int lj = (int)v.lnbr[k * np + gi];
+            const T sx = rn[(0 * MAXF + k) * np + gi], sy = rn[(1 * MAXF + k) * np + gi];
+#pragma unroll
+            for (int a = 1; a < FVLBM_Q; a++) {
+                const T en = T(EXA(a)) * nx + T(EYA(a)) * ny;
                 T face;
-                if (kind == SK_INTERIOR) {
-                    if (out) {
-                        face = fa + gxo * rx + gyo * ry;
-                    } else {
-                        const int lj = (int)tlnbr[sq];
-                        face = fs[a * lmax + lj] + gxs[(a - 1) * gmax + lj] * trn[sq] +
-                               gys[(a - 1) * gmax + lj] * trn[MAXF * TILE + sq];
-                    }
+                if (mask & (1u << (a - 1)))
+                    face = f[a] + gxs[(a - 1) * gmax + l] * rx + gys[(a - 1) * gmax + l] * ry;
+                else
+                    face = fs[a * lmax + lj] + gxs[(a - 1) * gmax + lj] * sx + gys[(a - 1) * gmax + lj] * sy;
+                flux[a] += en * (DEV ? face - f[a] : face);
+            }
+        } else {
+            const BcParam& b = v.bc[meta >> 16];
+            const T inv = T(1) / sqrt(nx * nx + ny * ny);
+#pragma unroll
+            for (int a = 1; a < FVLBM_Q; a++) {
+                const bool out = (mask >> (a - 1)) & 1u;
+                T face;
+                if (kind == SK_OUTLET && b.external) {
+                    face = f[a];
+                } else if ((kind == SK_INLET || kind == SK_OUTLET) && out) {
+                    face = f[a] + gxs[(a - 1) * gmax + l] * rx + gys[(a - 1) * gmax + l] * ry;
                 } else {
-                    const BcParam& b = v.bc[meta >> 16];
-                    if (kind == SK_OUTLET && b.external) {
-                        face = fa;
-                    } else if ((kind == SK_INLET || kind == SK_OUTLET) && out) {
-                        face = fa + gxo * rx + gyo * ry;
-                    } else {
-                        const T inv = T(1) / sqrt(nx * nx + ny * ny);
-                        const T d = bc_delta<T, DEV>(kind, b, a, fa, r, ux, uy, feqs<T, DEV>(a, r, ux, uy),
-                                                     nx * inv, ny * inv);
-                        face = kind == SK_SYMMETRY ? fa + T(0.5) * d : fa + d;
-                    }
+                    const T d = bc_delta<T, DEV>(kind, b, a, f[a], rho, ux, uy, feqs<T, DEV>(a, rho, ux, uy),
+                                                 nx * inv, ny * inv);
+                    face = kind == SK_SYMMETRY ? f[a] + T(0.5) * d : f[a] + d;
                 }
-                const T en = ea_x * nx + ea_y * ny;
-                flux += en * (DEV ? face - fa : face);
+                const T en = T(EXA(a)) * nx + T(EYA(a)) * ny;
+                flux[a] += en * (DEV ? face - f[a] : face);
             }
         }
-        const InstParam& P = v.inst[tgrp[l]];
-        const T rhs = -flux - (fa - feqs<T, DEV>(a, r, ux, uy)) * inst_inv_tau<T>(P);
-        const T dt = inst_dt<T>(P);
+    }
+    const T inv_tau = inst_inv_tau<T>(P);
+    const T dt = inst_dt<T>(P);
+    bool bad = false;
+    T* rp = (T*)v.rprev;
+#pragma unroll
+    for (int a = 0; a < FVLBM_Q; a++) {
+        const T rhs = -flux[a] - (f[a] - feqs<T, DEV>(a, rho, ux, uy)) * inv_tau;
         T outv;
         if (mode == MODE_RK) {
-            const T base = (fbase == fin) ? fa : Store<S>::ld(fbase, a * np + gi, P.inv_scale[a], P.off[a]);
+            const T base = (fbase == fin) ? f[a] : Store<S>::ld(fbase, a * np + gi, P.inv_scale[a], P.off[a]);
             outv = base + beta * dt * rhs;
         } else if (mode == MODE_AB2_FIRST) {
-            outv = fa + dt * rhs;
+            outv = f[a] + dt * rhs;
             rp[a * np + gi] = rhs;
         } else {
-            outv = fa + dt * (T(1.5) * rhs - T(0.5) * rp[a * np + gi]);
+            outv = f[a] + dt * (T(1.5) * rhs - T(0.5) * rp[a * np + gi]);
             rp[a * np + gi] = rhs;
         }
         bad |= !finite_val(outv);
@@ -434,6 +378,7 @@ __global__ void __launch_bounds__(8 * TILE) stage_tile_kernel(DevView v, const S
     }
     if (bad) *v.flag = 1;
 }
+
 
 static inline unsigned grid_of(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
@@ -452,7 +397,7 @@ static int tile_launch(const DevView& v, cudaStream_t st, const void* fin, const
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return fail(FVLBM_ERR_CUDA, "fused stage: %zu B shared memory: %s", smem, cudaGetErrorString(e));
     }
-    kern<<<(unsigned)v.n_tiles, 8 * TILE, smem, st>>>(v, (const S*)fin, (const S*)fbase, (S*)fout, (T)beta, mode);
+    kern<<<(unsigned)v.n_tiles, TILE, smem, st>>>(v, (const S*)fin, (const S*)fbase, (S*)fout, (T)beta, mode);
     return FVLBM_OK;
 }
 
@@ -460,8 +405,9 @@ template <typename T, typename S, int MAXF, bool DEV>
 static int tile_dispatch(const DevView& v, cudaStream_t st, const void* fin, const void* fbase, void* fout,
                          double beta, int mode) {
     switch (v.tile) {
-        case 64: return tile_launch<T, S, MAXF, DEV, 64>(v, st, fin, fbase, fout, beta, mode);
         case 128: return tile_launch<T, S, MAXF, DEV, 128>(v, st, fin, fbase, fout, beta, mode);
+        case 256: return tile_launch<T, S, MAXF, DEV, 256>(v, st, fin, fbase, fout, beta, mode);
+        case 512: return tile_launch<T, S, MAXF, DEV, 512>(v, st, fin, fbase, fout, beta, mode);
     }
     return fail(FVLBM_ERR_ARG, "unsupported tile size %d", v.tile);
 }

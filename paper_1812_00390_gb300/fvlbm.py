@@ -52,12 +52,30 @@ class MeshInfoT(C.Structure):
                 ("total_area", C.c_double), ("min_cfl_length", C.c_double)]
 
 
+class ServerConfigT(C.Structure):
+    _fields_ = [("device", C.c_int32), ("n_streams", C.c_int32), ("arena_bytes", C.c_size_t),
+                ("max_active", C.c_int32), ("check_interval", C.c_int32), ("residual_tol", C.c_double),
+                ("max_steps", C.c_int64)]
+
+
+class RequestInfoT(C.Structure):
+    _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("steps", C.c_int64), ("n_cell", C.c_int64),
+                ("residual", C.c_double), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double), ("workspace_bytes", C.c_size_t)]
+
+
+class ServerStatsT(C.Structure):
+    _fields_ = [("queued", C.c_int32), ("active", C.c_int32), ("arena_free", C.c_size_t),
+                ("arena_free_largest", C.c_size_t), ("cell_steps", C.c_int64), ("t_now", C.c_double)]
+
+
 #: every symbol include/fvlbm.h declares
 EXPORTS = ["fvlbm_mesh_create", "fvlbm_mesh_concat", "fvlbm_mesh_destroy", "fvlbm_mesh_info",
            "fvlbm_suggest_dt", "fvlbm_workspace_bytes", "fvlbm_init", "fvlbm_step", "fvlbm_macros",
            "fvlbm_residual", "fvlbm_mass", "fvlbm_mass_noalloc", "fvlbm_get_f", "fvlbm_set_f", "fvlbm_sync",
            "fvlbm_get_dt", "fvlbm_profile", "fvlbm_launches_per_step", "fvlbm_solver_destroy",
-           "fvlbm_last_error"]
+           "fvlbm_server_create", "fvlbm_server_submit", "fvlbm_server_poll", "fvlbm_server_request",
+           "fvlbm_server_stats", "fvlbm_server_destroy", "fvlbm_last_error"]
 
 
 def _load():
@@ -91,6 +109,12 @@ def _load():
         "fvlbm_profile": [P, C.c_int64, dp, C.c_int32, i32p, i64p],
         "fvlbm_launches_per_step": [P, i64p],
         "fvlbm_solver_destroy": [P],
+        "fvlbm_server_create": [C.POINTER(ServerConfigT), PP],
+        "fvlbm_server_submit": [P, P, C.POINTER(ParamsT), C.c_int32, i64p],
+        "fvlbm_server_poll": [P, i32p],
+        "fvlbm_server_request": [P, C.c_int64, C.POINTER(RequestInfoT), dp, dp],
+        "fvlbm_server_stats": [P, C.POINTER(ServerStatsT)],
+        "fvlbm_server_destroy": [P],
         "fvlbm_last_error": [],
     }
     for name, args in sig.items():
@@ -99,6 +123,7 @@ def _load():
         fn.restype = C.c_int
     lib.fvlbm_mesh_destroy.restype = None
     lib.fvlbm_solver_destroy.restype = None
+    lib.fvlbm_server_destroy.restype = None
     lib.fvlbm_last_error.restype = C.c_char_p
     return lib
 
@@ -288,6 +313,61 @@ class Solver:
         h = getattr(self, "_h", None)
         if h is not None and h.value:
             lib.fvlbm_solver_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+REQ_QUEUED, REQ_ACTIVE, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+
+
+class Server:
+    """Continuous-batching solve server on one GPU (see fvlbm_server_* in the header)."""
+
+    def __init__(self, arena_bytes: int, device: int = 0, n_streams: int = 4, max_active: int = 16,
+                 check_interval: int = 1000, residual_tol: float = 1e-8, max_steps: int = 20000):
+        cfg = ServerConfigT(device, n_streams, int(arena_bytes), max_active, check_interval, residual_tol, max_steps)
+        h = C.c_void_p()
+        _check(lib.fvlbm_server_create(C.byref(cfg), C.byref(h)))
+        self._h = h
+        self._meshes = {}
+
+    def submit(self, mesh: Mesh, params) -> int:
+        plist = [params] if isinstance(params, ParamsT) else list(params)
+        arr = (ParamsT * len(plist))(*plist)
+        rid = C.c_int64()
+        _check(lib.fvlbm_server_submit(self._h, mesh._h, arr, len(plist), C.byref(rid)))
+        self._meshes[rid.value] = mesh          # the mesh must outlive the request
+        return rid.value
+
+    def poll(self) -> int:
+        n = C.c_int32()
+        _check(lib.fvlbm_server_poll(self._h, C.byref(n)))
+        return n.value
+
+    def request(self, rid: int, fields: bool = False):
+        info = RequestInfoT()
+        _check(lib.fvlbm_server_request(self._h, rid, C.byref(info), None, None))
+        d = {k: getattr(info, k) for k, _ in RequestInfoT._fields_}
+        if fields and info.state == REQ_DONE:
+            rho = np.zeros(info.n_cell)
+            u = np.zeros((info.n_cell, 2))
+            _check(lib.fvlbm_server_request(self._h, rid, C.byref(info), _d(rho), _d(u)))
+            d["rho"], d["u"] = rho, u
+        if info.state in (REQ_DONE, REQ_FAILED):
+            self._meshes.pop(rid, None) if fields else None
+        return d
+
+    def stats(self) -> dict:
+        st = ServerStatsT()
+        _check(lib.fvlbm_server_stats(self._h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStatsT._fields_}
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib.fvlbm_server_destroy(h)
             self._h = None
 
     def __del__(self):

@@ -86,7 +86,7 @@ def test_fp64_parity_every_mesh_and_scheme(fv, orc, name, scheme):
     s.close()
 
 
-@pytest.mark.parametrize("kernel", [1, 64, 128])
+@pytest.mark.parametrize("kernel", [1, 128, 256, 512])
 @pytest.mark.parametrize("name", ["cylinder", "bricks", "internal_io", "two_tri_periodic", "cavity_tri"])
 def test_stage_kernel_variants(fv, orc, name, kernel):
     """Two-kernel stage and fused stage (each tile size) against the oracle in
@@ -112,13 +112,13 @@ def test_stage_kernel_variants(fv, orc, name, kernel):
 
 def test_fused_tiles_span_instances(fv):
     """Tiles that straddle instance boundaries give the same state as the
-    two-kernel stage (instances of 2 to 3750 cells, tile 128)."""
+    two-kernel stage (instances of 2 to 3750 cells, tile 512)."""
     meshes = [mg.two_triangles(), mg.couette(8, 3), mg.cavity(10, 3.0), mg.two_triangles(periodic=True),
               mg.cylinder_hybrid(n_rad=25, n_circ=50, n_tri_rings=25, seed=3), mg.bricks(6, 4)]
     hs = [fv.Mesh(m) for m in meshes]
     taus = [0.2, 0.24, 0.05, 0.3, 0.02, 0.1]
     out = []
-    for kernel in (1, 128):
+    for kernel in (1, 512):
         s = fv.Solver(fv.Mesh.concat(hs), [fv.make_params(t, scheme="rk4", precision="fp64", kernel=kernel,
                                                           u0=(0.02, 0.0)) for t in taus])
         s.step(12)

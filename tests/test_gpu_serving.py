@@ -1,0 +1,104 @@
+"""Continuous-batching server: requests admitted by device-memory budget while
+others run, overlapping on the GPU, each with the same result as when solved
+alone."""
+import numpy as np
+import pytest
+
+from paper_1812_00390_gb300 import meshgen as mg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fv():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1812_00390_gb300 import fvlbm
+    return fvlbm
+
+
+def _meshes():
+    return [mg.cylinder_hybrid(n_rad=12, n_circ=40, first=0.01, growth=1.15, r_far=8.0, n_tri_rings=12, seed=1),
+            mg.tandem_cylinders(gap_ratio=2.5, n_circ=48, grade=0.25, r_far=8.0, seed=2),
+            mg.cavity(24, 5.0),
+            mg.couette(16, 6),
+            mg.tandem_cylinders(gap_ratio=4.0, n_circ=40, grade=0.3, r_far=8.0, seed=3),
+            mg.cylinder_hybrid(n_rad=8, n_circ=32, first=0.02, growth=1.2, r_far=6.0, n_tri_rings=8, seed=4)]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_each_result_same_alone_and_in_the_mix(fv, prec):
+    meshes = _meshes()
+    taus = [0.01, 0.012, 0.05, 0.24, 0.015, 0.02]
+    u0 = [(0.05, 0.0), (0.05, 0.0), (0.0, 0.0), (0.0, 0.0), (0.05, 0.0), (0.05, 0.0)]
+    handles = [fv.Mesh(m) for m in meshes]
+    params = [fv.make_params(t, scheme="rk2", precision=prec, u0=u) for t, u in zip(taus, u0)]
+    need = [fv.Solver(h, p).workspace_bytes for h, p in zip(handles, params)]
+    # room for about two requests at a time: later ones wait for memory
+    arena = int(sorted(need)[-1] + sorted(need)[-2] + 4096)
+    srv = fv.Server(arena, n_streams=3, max_active=4, check_interval=50, residual_tol=0.0, max_steps=200)
+    ids = [srv.submit(h, p) for h, p in zip(handles, params)]
+    done = 0
+    rounds = 0
+    while done < len(ids):
+        done += srv.poll()
+        st = srv.stats()
+        assert st["active"] <= 4
+        rounds += 1
+        assert rounds < 1000
+    infos = [srv.request(i, fields=True) for i in ids]
+    for k, info in enumerate(infos):
+        assert info["state"] == fv.REQ_DONE, info
+        assert info["steps"] == 200
+        solo = fv.Solver(handles[k], params[k])
+        solo.step(200)
+        rho, u = solo.macros()
+        np.testing.assert_array_equal(info["rho"], rho)
+        np.testing.assert_array_equal(info["u"], u)
+    # the budget held: at no time were the admitted requests' workspaces above the arena
+    events = sorted([(x["t_admit"], x["workspace_bytes"]) for x in infos] +
+                    [(x["t_done"], -x["workspace_bytes"]) for x in infos])
+    used = 0
+    for _, b in events:
+        used += b
+        assert used <= arena
+    # some request waited for memory and was admitted when an earlier one finished,
+    # while another was still running
+    first_done = min(x["t_done"] for x in infos)
+    late = [x for x in infos if x["t_admit"] >= first_done]
+    assert late
+    assert any(y["t_admit"] < x["t_admit"] < y["t_done"] for x in late for y in infos)
+    assert srv.stats()["arena_free"] == arena
+    srv.close()
+
+
+def test_residual_stop_and_errors(fv):
+    m = mg.cavity(12, 3.0, U=0.0)          # fluid at rest stays at rest: residual 0 at once
+    h = fv.Mesh(m)
+    srv = fv.Server(1 << 26, check_interval=10, residual_tol=1e-8, max_steps=10000)
+    rid = srv.submit(h, fv.make_params(0.1, scheme="euler", precision="fp32"))
+    while srv.poll() == 0:
+        pass
+    info = srv.request(rid)
+    assert info["state"] == fv.REQ_DONE and info["steps"] == 10 and info["residual"] == 0.0
+    big = fv.Mesh(mg.cavity(64, 5.0))
+    with pytest.raises(fv.FvlbmError) as e:
+        fv.Server(1 << 16).submit(big, fv.make_params(0.1))
+    assert e.value.name == "OOM"
+    srv.close()
+
+
+def test_poisson_driver_small(fv):
+    from paper_1812_00390_gb300 import serving
+    specs = serving.request_mix(6, seed=390, rate=50.0, tandem_cells=(3000, 5000), single_cells=(2000, 3000))
+    meshes = [mg.tandem_cylinders(gap_ratio=s.gap, n_circ=48, grade=0.3, r_far=8.0, seed=1) if s.kind == "tandem"
+              else mg.cylinder_hybrid(n_rad=10, n_circ=40, first=0.01, growth=1.15, r_far=8.0, n_tri_rings=10)
+              for s in specs]
+    srv = fv.Server(1 << 30, check_interval=100, residual_tol=1e-8, max_steps=400)
+    lat, infos, wall, cells = serving.run_poisson(srv, fv, specs, meshes)
+    s = serving.summarize(lat, wall, cells)
+    assert s["requests"] == 6 and s["p99_s"] >= s["p50_s"] > 0 and s["aggregate_mcups"] > 0
+    assert all(x["state"] == fv.REQ_DONE for x in infos)
+    srv.close()
