@@ -169,7 +169,7 @@ def measured_peaks():
 
 
 def kernel_source_sha() -> str:
-    src = os.path.join(ROOT, "paper_1812_00390_gb300", "csrc", "fvlbm_kernels.cu")
+    src = os.path.join(ROOT, "paper_1812_00390_gb300", "csrc", "fvlbm_stage.cuh")
     return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
 
 
