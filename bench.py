@@ -77,11 +77,21 @@ def batch_instances(n_inst: int, seed: int = 2018, small: bool = False, rank: in
     return variants, out
 
 
-def build_solver(fv, variants, inst, precision, scheme="rk2", handles=None):
+def build_solver(fv, variants, inst, precision, scheme="rk2", handles=None, kernel=0):
     handles = handles or {k: fv.Mesh(m) for k, m in variants.items()}
     mesh = fv.Mesh.concat([handles[k] for k, _, _ in inst])
-    params = [fv.make_params(tau, scheme=scheme, precision=precision, u0=u0) for _, tau, u0 in inst]
+    params = [fv.make_params(tau, scheme=scheme, precision=precision, u0=u0, kernel=kernel)
+              for _, tau, u0 in inst]
     return fv.Solver(mesh, params), handles
+
+
+def tune_kernel(fv, handles, inst, precision, scheme="rk2", n_sample=12, steps=10):
+    """Stage-kernel variant chosen by the library's autotuner on the first
+    n_sample instances of the batch (all three kinds)."""
+    sub = inst[:n_sample]
+    mesh = fv.Mesh.concat([handles[k] for k, _, _ in sub])
+    params = [fv.make_params(tau, scheme=scheme, precision=precision, u0=u0) for _, tau, u0 in sub]
+    return fv.autotune(mesh, params, steps=steps)
 
 
 # ----------------------------------------------------------------------------- ranks
@@ -281,7 +291,9 @@ def run_ours(args):
         v, thr, sample, _, _, _ = oracle_mcups(variants, inst, args.cpu_seconds)
         cpu = {"value": v, "unit": "MCUPS", "cores": thr, "kind": "oracle", "sample": sample}
 
-    s32, handles = build_solver(fv, variants, inst, "fp32")
+    handles = {k: fv.Mesh(m) for k, m in variants.items()}
+    kernel32, tune32 = tune_kernel(fv, handles, inst, "fp32")
+    s32, _ = build_solver(fv, variants, inst, "fp32", handles=handles, kernel=kernel32)
     n_cells = s32.n_cell
     stream = s32.stream
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -319,17 +331,18 @@ def run_ours(args):
     err = None
     if not args.no_fp64:
         k64 = max(3, args.steps // 8)
-        s64, _ = build_solver(fv, variants, inst, "fp64", handles=handles)
+        kernel64, tune64 = tune_kernel(fv, handles, inst, "fp64")
+        s64, _ = build_solver(fv, variants, inst, "fp64", handles=handles, kernel=kernel64)
         ms64, _ = timed(s64, k64)
         ms64 /= k64
         # same number of steps from Step 0 in both modes
         n_cmp = args.warmup + args.steps + args.steps
         s64.close()
-        s64, _ = build_solver(fv, variants, inst, "fp64", handles=handles)
+        s64, _ = build_solver(fv, variants, inst, "fp64", handles=handles, kernel=kernel64)
         s64.step(n_cmp)
         _, u64 = s64.macros()
         s64.close()
-        ref32, _ = build_solver(fv, variants, inst, "fp32", handles=handles)
+        ref32, _ = build_solver(fv, variants, inst, "fp32", handles=handles, kernel=kernel32)
         ref32.step(n_cmp)
         _, u32 = ref32.macros()
         ref32.close()
@@ -372,6 +385,24 @@ def run_ours(args):
         e2e_s = time.perf_counter() - t0
         e2e_val = n_cells * world * e2e_inner * args.e2e_steps / e2e_s / 1e6
 
+    # serving stream (config 5): Poisson arrivals of tandem / single cylinder
+    # solves on the continuous-batching server, p50 / p99 time to completion
+    serving = None
+    if args.serving > 0 and rank == 0:
+        from paper_1812_00390_gb300 import serving as sv
+        specs = sv.request_mix(args.serving, seed=390, rate=args.serving_rate)
+        meshes = [sv.build_mesh(sp) for sp in specs]
+        srv = fv.Server(int(args.serving_arena_gb * 1e9), device=dev, n_streams=8, max_active=32,
+                        check_interval=1000, residual_tol=1e-8, max_steps=args.serving_steps)
+        lat, infos, wall, cells = sv.run_poisson(srv, fv, specs, meshes)
+        serving = sv.summarize(lat, wall, cells)
+        serving.update({"arrival_rate_per_s": args.serving_rate, "precision": "fp32", "scheme": "rk2",
+                        "stop": f"residual <= 1e-8 (checked every 1000 steps) or {args.serving_steps} steps",
+                        "cells_per_request": [int(m.n_cell) for m in meshes],
+                        "converged": int(sum(1 for x in infos if x["residual"] <= 1e-8)),
+                        "arena_gb": args.serving_arena_gb})
+        srv.close()
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MCUPS", "n_gpus": world, "steps": args.steps,
@@ -380,9 +411,11 @@ def run_ours(args):
             "config": {"workload": args.workload, "n_instances": args.instances, "n_cells": n_cells,
                        "scheme": "rk2", "precision": "fp32 deviation (g = f - w)",
                        "l2": "inputs larger than L2 (f state %.0f MB per GPU)" % (n_cells * 9 * 4 / 1e6),
-                       "parallelism": "instances replicated per GPU (weak scaling)" if world > 1 else "1 GPU"},
+                       "parallelism": "instances replicated per GPU (weak scaling)" if world > 1 else "1 GPU",
+                       "stage_kernel": kernel32,
+                       "autotune_ms_per_step": {str(k): v for k, v in tune32.items()}},
             "fp64": {"value": (n_cells * world / (ms64 / 1e3) / 1e6) if ms64 else None, "unit": "MCUPS",
-                     "ms_per_step": ms64},
+                     "ms_per_step": ms64, "stage_kernel": kernel64 if ms64 else None},
             "mixed_over_fp64": (value / (n_cells * world / (ms64 / 1e3) / 1e6)) if ms64 else None,
             "mixed_error_vs_fp64": ({"max_rel_velocity": err, "steps": err_steps} if err is not None else None),
             "roofline": roof,
@@ -391,6 +424,7 @@ def run_ours(args):
                      "d2h_bytes_per_step": 8 * args.instances + 4,
                      "definition": f"set_f from host + {e2e_inner} time steps + residual read-back"}
                     if e2e_val is not None else None),
+            "serving": serving,
             "gpu_launches": launches,
             "clocks": clocks,
         }
@@ -411,6 +445,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--e2e-inner", type=int, default=100)
+    ap.add_argument("--serving", type=int, default=8, help="requests in the serving leg (0 = skip)")
+    ap.add_argument("--serving-rate", type=float, default=2.0, help="Poisson arrivals per second")
+    ap.add_argument("--serving-steps", type=int, default=20000)
+    ap.add_argument("--serving-arena-gb", type=float, default=8.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     args = ap.parse_args()

@@ -264,6 +264,20 @@ int fvlbm_get_dt(const fvlbm_solver* s, int32_t instance, double* dt);
 int fvlbm_profile(fvlbm_solver* s, int64_t n, double* avg_ms, int32_t max_kinds, int32_t* n_kinds,
                   int64_t* launches);
 
+/*
+ * Autotuner: time every stage-kernel variant (params.kernel = 1, 128, 256,
+ * 512; variants that do not fit are skipped) on this mesh and parameters for
+ * `steps` steps after 2 warm-up steps, each in a temporary solver whose
+ * workspace the library allocates and frees, and report the fastest.
+ *   stream       as for fvlbm_init
+ *   best_kernel  host, written: the value to put in fvlbm_params.kernel
+ *   ms_per_step  host [4] or NULL: device ms per step of each variant in the
+ *                order above (+inf when skipped)
+ * Errors: FVLBM_ERR_ARG, _CUDA, _UNSUPPORTED (no variant fits).
+ */
+int fvlbm_autotune(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t n_params, void* stream,
+                   int32_t steps, int32_t* best_kernel, double* ms_per_step);
+
 /* Kernels one time step launches (host, written). */
 int fvlbm_launches_per_step(const fvlbm_solver* s, int64_t* launches);
 

@@ -37,7 +37,13 @@ struct fvlbm_solver {
     std::vector<InstParam> inst;
     bool ab2_started = false;
     std::vector<double> h_conv, h_rho, h_ux, h_uy;
+    // CUDA graphs of one step and of GRAPH_CHUNK steps, built lazily
+    cudaGraphExec_t g1 = nullptr, gk = nullptr;
+    bool graphs_ok = true;
+    int64_t direct_steps = 0;
 };
+
+static constexpr int64_t GRAPH_CHUNK = 32;
 
 namespace {
 
@@ -542,6 +548,8 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
 
 extern "C" void fvlbm_solver_destroy(fvlbm_solver* s) {
     if (!s) return;
+    if (s->g1) cudaGraphExecDestroy(s->g1);
+    if (s->gk) cudaGraphExecDestroy(s->gk);
     if (s->own_ws && s->ws) {
         DeviceGuard dg(s->device);
         cudaStreamSynchronize(s->stream);
@@ -647,12 +655,59 @@ extern "C" int fvlbm_launches_per_step(const fvlbm_solver* s, int64_t* launches)
     return FVLBM_OK;
 }
 
+// Capture `nsteps` steps of the solver's stream into an executable graph.
+static bool build_graph(fvlbm_solver* s, int64_t nsteps, cudaGraphExec_t* out) {
+    if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int rc = FVLBM_OK;
+    for (int64_t k = 0; k < nsteps && rc == FVLBM_OK; k++) rc = enqueue_step(s);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+    bool ok = rc == FVLBM_OK && e == cudaSuccess && g;
+    if (ok) ok = cudaGraphInstantiate(out, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+        *out = nullptr;
+        cudaGetLastError();
+        clear_error();
+    }
+    return ok;
+}
+
+// Steps are replayed from CUDA graphs (chunks of GRAPH_CHUNK, then single
+// steps) once the solver has run directly at least once (so that kernel
+// attributes are set outside capture) and AB2 has its history; the legacy
+// default stream cannot be captured and always launches directly.
 extern "C" int fvlbm_step(fvlbm_solver* s, int64_t n) {
     clear_error();
     if (!s || n < 0) return fail(FVLBM_ERR_ARG, "fvlbm_step: bad arguments");
     DeviceGuard dg(s->device);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s->stream, &cs);
+    bool graphs = s->graphs_ok && s->stream != nullptr && cs == cudaStreamCaptureStatusNone &&
+                  s->direct_steps > 0 && (s->scheme != FVLBM_AB2 || s->ab2_started);
+    if (graphs && !s->g1) {
+        if (!build_graph(s, 1, &s->g1) || !build_graph(s, GRAPH_CHUNK, &s->gk)) {
+            s->graphs_ok = false;
+            graphs = false;
+        }
+    }
+    while (graphs && n >= GRAPH_CHUNK) {
+        cudaError_t e = cudaGraphLaunch(s->gk, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "fvlbm_step: graph launch");
+        n -= GRAPH_CHUNK;
+    }
     for (int64_t k = 0; k < n; k++) {
-        int rc = enqueue_step(s);
+        int rc;
+        if (graphs) {
+            cudaError_t e = cudaGraphLaunch(s->g1, s->stream);
+            rc = e == cudaSuccess ? FVLBM_OK : cuda_fail(e, "fvlbm_step: graph launch");
+        } else {
+            rc = enqueue_step(s);
+            s->direct_steps++;
+        }
         if (rc) return rc;
     }
     return FVLBM_OK;
@@ -775,6 +830,7 @@ extern "C" int fvlbm_set_f(fvlbm_solver* s, const double* f) {
     int rc = launch_set_f(s->v, s->prec, s->stream);
     if (rc) return rc;
     s->ab2_started = false;
+    if (s->scheme == FVLBM_AB2) s->direct_steps = 0;   // the next step is an Euler start, launched directly
     CK(cudaStreamSynchronize(s->stream), "synchronise");
     return FVLBM_OK;
 }
@@ -783,5 +839,51 @@ extern "C" int fvlbm_get_dt(const fvlbm_solver* s, int32_t instance, double* dt)
     clear_error();
     if (!s || !dt || instance < 0 || instance >= s->n_inst) return fail(FVLBM_ERR_ARG, "fvlbm_get_dt: bad arguments");
     *dt = s->inst[instance].dt;
+    return FVLBM_OK;
+}
+
+extern "C" int fvlbm_autotune(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t n_params, void* stream,
+                              int32_t steps, int32_t* best_kernel, double* ms_per_step) {
+    clear_error();
+    if (!mesh || !params || n_params <= 0 || steps <= 0 || !best_kernel)
+        return fail(FVLBM_ERR_ARG, "fvlbm_autotune: bad arguments");
+    static const int32_t cand[4] = {1, 128, 256, 512};
+    std::vector<fvlbm_params> p(params, params + n_params);
+    double best = INFINITY;
+    int32_t pick = 0;
+    for (int c = 0; c < 4; c++) {
+        if (ms_per_step) ms_per_step[c] = INFINITY;
+        for (auto& q : p) q.kernel = cand[c];
+        fvlbm_solver* sv = nullptr;
+        int rc = fvlbm_init(mesh, p.data(), n_params, stream, nullptr, 0, &sv);
+        if (rc == FVLBM_ERR_UNSUPPORTED || rc == FVLBM_ERR_OOM) continue;   // variant does not fit
+        if (rc) return rc;
+        DeviceGuard dg(sv->device);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        float ms = 0;
+        rc = fvlbm_step(sv, 2);
+        if (!rc) rc = fvlbm_sync(sv);
+        if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+            rc = fail(FVLBM_ERR_CUDA, "fvlbm_autotune: events");
+        if (!rc) {
+            cudaEventRecord(e0, sv->stream);
+            rc = fvlbm_step(sv, steps);
+            cudaEventRecord(e1, sv->stream);
+            if (!rc) rc = fvlbm_sync(sv);
+            if (!rc) cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        fvlbm_solver_destroy(sv);
+        if (rc) return rc;
+        const double per = ms / steps;
+        if (ms_per_step) ms_per_step[c] = per;
+        if (per < best) {
+            best = per;
+            pick = cand[c];
+        }
+    }
+    if (!pick) return fail(FVLBM_ERR_UNSUPPORTED, "fvlbm_autotune: no stage kernel variant fits");
+    *best_kernel = pick;
     return FVLBM_OK;
 }

@@ -73,7 +73,7 @@ class ServerStatsT(C.Structure):
 EXPORTS = ["fvlbm_mesh_create", "fvlbm_mesh_concat", "fvlbm_mesh_destroy", "fvlbm_mesh_info",
            "fvlbm_suggest_dt", "fvlbm_workspace_bytes", "fvlbm_init", "fvlbm_step", "fvlbm_macros",
            "fvlbm_residual", "fvlbm_mass", "fvlbm_mass_noalloc", "fvlbm_get_f", "fvlbm_set_f", "fvlbm_sync",
-           "fvlbm_get_dt", "fvlbm_profile", "fvlbm_launches_per_step", "fvlbm_solver_destroy",
+           "fvlbm_get_dt", "fvlbm_profile", "fvlbm_autotune", "fvlbm_launches_per_step", "fvlbm_solver_destroy",
            "fvlbm_server_create", "fvlbm_server_submit", "fvlbm_server_poll", "fvlbm_server_request",
            "fvlbm_server_stats", "fvlbm_server_destroy", "fvlbm_last_error"]
 
@@ -108,6 +108,7 @@ def _load():
         "fvlbm_get_dt": [P, C.c_int32, dp],
         "fvlbm_profile": [P, C.c_int64, dp, C.c_int32, i32p, i64p],
         "fvlbm_launches_per_step": [P, i64p],
+        "fvlbm_autotune": [P, C.POINTER(ParamsT), C.c_int32, P, C.c_int32, i32p, dp],
         "fvlbm_solver_destroy": [P],
         "fvlbm_server_create": [C.POINTER(ServerConfigT), PP],
         "fvlbm_server_submit": [P, P, C.POINTER(ParamsT), C.c_int32, i64p],
@@ -236,7 +237,9 @@ class Solver:
         self.n_cell = mesh.n_cell
         self.n_inst = mesh.info()["n_instances"]
         if stream is None:
-            stream = torch.cuda.current_stream(dev)
+            # a stream of its own (not the legacy default stream, which cannot
+            # be captured into the CUDA graphs fvlbm_step replays)
+            stream = torch.cuda.Stream(device=dev)
         self.stream = stream
         sh = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
         nbytes = C.c_size_t()
@@ -317,6 +320,23 @@ class Solver:
 
     def __del__(self):
         self.close()
+
+
+KERNEL_VARIANTS = (1, 128, 256, 512)
+
+
+def autotune(mesh: Mesh, params, steps: int = 10, stream=None):
+    """Fastest stage-kernel variant for this mesh: (params.kernel value, {variant: ms per step})."""
+    import torch
+    plist = [params] if isinstance(params, ParamsT) else list(params)
+    arr = (ParamsT * len(plist))(*plist)
+    if stream is None:
+        stream = torch.cuda.Stream(device=plist[0].device)
+    sh = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+    best = C.c_int32()
+    ms = np.zeros(4)
+    _check(lib.fvlbm_autotune(mesh._h, arr, len(plist), C.c_void_p(sh), steps, C.byref(best), _d(ms)))
+    return best.value, dict(zip(KERNEL_VARIANTS, ms.tolist()))
 
 
 REQ_QUEUED, REQ_ACTIVE, REQ_DONE, REQ_FAILED = 0, 1, 2, 3

@@ -273,3 +273,34 @@ def test_edge_cases(fv, orc):
     with pytest.raises(fv.FvlbmError) as e:
         s.sync()
     assert e.value.name == "DIVERGED"
+
+
+@pytest.mark.parametrize("scheme", ["rk2", "ab2", "euler"])
+def test_graph_replay_matches_direct_launches(fv, scheme):
+    """fvlbm_step replays CUDA graphs of 32 steps and of 1 step; the state is
+    bitwise the same as with one step per call, also across an AB2 restart."""
+    m = mg.cylinder_hybrid(n_rad=8, n_circ=32, first=0.02, growth=1.15, r_far=8.0, n_tri_rings=8, seed=4)
+    p = fv.make_params(0.02, scheme=scheme, precision="fp32", u0=(0.05, 0.0))
+    a, b = fv.Solver(fv.Mesh(m), p), fv.Solver(fv.Mesh(m), p)
+    for _ in range(70):
+        a.step(1)
+    b.step(70)
+    assert np.array_equal(a.get_f(), b.get_f())
+    f = a.get_f()
+    a.set_f(f)
+    b.set_f(f)
+    for _ in range(40):
+        a.step(1)
+    b.step(3)
+    b.step(37)
+    assert np.array_equal(a.get_f(), b.get_f())
+
+
+def test_autotune_picks_a_variant(fv):
+    m = mg.cavity(48, 5.0)
+    best, ms = fv.autotune(fv.Mesh(m), fv.make_params(0.05, scheme="rk2", precision="fp32"), steps=5)
+    assert best in fv.KERNEL_VARIANTS
+    assert ms[best] == min(ms.values()) and np.isfinite(ms[best]) and ms[best] > 0
+    s = fv.Solver(fv.Mesh(m), fv.make_params(0.05, scheme="rk2", precision="fp32", kernel=best))
+    s.step(3)
+    s.sync()
