@@ -295,7 +295,6 @@ def run_ours(args):
     kernel32, tune32 = tune_kernel(fv, handles, inst, "fp32")
     s32, _ = build_solver(fv, variants, inst, "fp32", handles=handles, kernel=kernel32)
     n_cells = s32.n_cell
-    stream = s32.stream
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def barrier():
@@ -308,10 +307,10 @@ def run_ours(args):
         solver.sync()
         barrier()
         with ClockSampler(dev) as clk:
-            start.record(stream)
+            start.record(solver.stream)        # events on the stream the solver launches on
             for _ in range(k):
                 solver.step(1)
-            end.record(stream)
+            end.record(solver.stream)
             end.synchronize()
         ms = start.elapsed_time(end)
         solver.sync()

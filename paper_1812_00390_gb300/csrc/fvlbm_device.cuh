@@ -18,35 +18,141 @@ __device__ __forceinline__ T wgt(int a) {
     return a == 0 ? T(4.0 / 9.0) : (a < 5 ? T(1.0 / 9.0) : T(1.0 / 36.0));
 }
 
+// Density and velocity (Sec. 2.1).  FP64 mode: r = rho = sum f.  Deviation
+// mode: r = rho - 1 = sum g, kept unrounded by the 1 so that the density
+// deviation keeps FP32 relative precision.
+template <typename T, bool DEV>
+__device__ __forceinline__ void moments(const T* f, T& r, T& ux, T& uy) {
+    T s = 0, mx = 0, my = 0;
+#pragma unroll
+    for (int a = 0; a < FVLBM_Q; a++) {
+        s += f[a];
+        mx += T(EXA(a)) * f[a];
+        my += T(EYA(a)) * f[a];
+    }
+    r = s;
+    const T rho = DEV ? T(1) + s : s;
+    ux = mx / rho;
+    uy = my / rho;
+}
+
+// Eq. (feq).  FP64 mode: r = rho, returns f^eq.  Deviation mode: r = rho - 1,
+// returns f^eq - w = w [(rho - 1) + rho (3 e.u + 4.5 (e.u)^2 - 1.5 u^2)].
+template <typename T, bool DEV>
+__device__ __forceinline__ T feqs(int a, T r, T ux, T uy) {
+    T eu = T(EXA(a)) * ux + T(EYA(a)) * uy;
+    T uu = ux * ux + uy * uy;
+    T poly = T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu;
+    if (DEV) return wgt<T>(a) * (r + (T(1) + r) * poly);
+    return r * wgt<T>(a) * (T(1) + poly);
+}
+
+// Density argument of feqs for a given density.
+template <typename T, bool DEV>
+__device__ __forceinline__ T rarg(double rho) { return DEV ? T(rho - 1.0) : T(rho); }
+
 // ------------------------------------------------------------------ storage
-template <typename S> struct Store;
-// FP64 / FP32 keep the value itself.
-template <> struct Store<double> {
-    __device__ static double ld(const double* p, int64_t i, float, float) { return p[i]; }
-    __device__ static void st(double* p, int64_t i, double v, float, float) { p[i] = v; }
-};
-template <> struct Store<float> {
-    __device__ static float ld(const float* p, int64_t i, float, float) { return p[i]; }
-    __device__ static void st(float* p, int64_t i, float v, float, float) { p[i] = v; }
-};
-// 16-bit storage keeps (g - off) * scale: off is the deviation of the
-// instance's initial equilibrium, so the stored number is the departure from
-// it and the format's relative precision applies to that departure.
-template <> struct Store<__half> {
-    __device__ static float ld(const __half* p, int64_t i, float inv_scale, float off) {
-        return fmaf(__half2float(p[i]), inv_scale, off);
+// Whole-cell access to the stored state (T: arithmetic type, DEV: deviation
+// mode, the stored quantity is g = f - w).
+//  double / float   plane a (a = 0..8) holds g_a (f_a in FP64 mode).
+//  __half / bf16    split format: planes 0..2 hold rho - 1, rho u_x, rho u_y in
+//                   FP32; the next six 16-bit planes hold the non-equilibrium
+//                   parts n_a = g_a - g^eq_a(rho, u) of directions a = 3..8,
+//                   times a power-of-two scale per (instance, direction).
+//                   n_0, n_1, n_2 follow from sum_a n_a = 0 and
+//                   sum_a e_a n_a = 0 (the non-equilibrium part carries no mass
+//                   or momentum), so rho and u never round through 16 bits;
+//                   only the small non-equilibrium part does.
+template <typename S> struct CellIO;
+
+template <typename S> struct PlainIO {
+    template <typename T, bool DEV>
+    __device__ static void load(const void* base, int64_t i, int64_t np, const InstParam&, T* f) {
+        const S* p = (const S*)base;
+#pragma unroll
+        for (int a = 0; a < FVLBM_Q; a++) f[a] = (T)p[a * np + i];
     }
-    __device__ static void st(__half* p, int64_t i, float v, float scale, float off) {
-        p[i] = __float2half_rn((v - off) * scale);
+    template <typename T, bool DEV>
+    __device__ static void store(void* base, int64_t i, int64_t np, const InstParam&, const T* f) {
+        S* p = (S*)base;
+#pragma unroll
+        for (int a = 0; a < FVLBM_Q; a++) p[a * np + i] = (S)f[a];
     }
+    // FP64 moments of the stored state: r = sum f (FP64 mode) or sum g (deviation), j = sum e g
+    __device__ static void moments64(const void* base, int64_t i, int64_t np, const InstParam&, double& r, double& jx,
+                                     double& jy) {
+        const S* p = (const S*)base;
+        r = jx = jy = 0;
+        for (int a = 0; a < FVLBM_Q; a++) {
+            const double x = (double)p[a * np + i];
+            r += x;
+            jx += EXA(a) * x;
+            jy += EYA(a) * x;
+        }
+    }
+    static constexpr size_t bytes_per_cell = FVLBM_Q * sizeof(S);
 };
-template <> struct Store<__nv_bfloat16> {
-    __device__ static float ld(const __nv_bfloat16* p, int64_t i, float, float off) {
-        return __bfloat162float(p[i]) + off;
+template <> struct CellIO<double> : PlainIO<double> {};
+template <> struct CellIO<float> : PlainIO<float> {};
+
+template <typename H> __device__ __forceinline__ float h2f(H x);
+template <> __device__ __forceinline__ float h2f<__half>(__half x) { return __half2float(x); }
+template <> __device__ __forceinline__ float h2f<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <typename H> __device__ __forceinline__ H f2h(float x);
+template <> __device__ __forceinline__ __half f2h<__half>(float x) { return __float2half_rn(x); }
+template <> __device__ __forceinline__ __nv_bfloat16 f2h<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+
+template <typename H> struct SplitIO {
+    template <typename T, bool DEV>
+    __device__ static void load(const void* base, int64_t i, int64_t np, const InstParam& P, T* f) {
+        const float* c = (const float*)base;
+        const H* h = (const H*)(c + 3 * np);
+        const float dr = c[i], jx = c[np + i], jy = c[2 * np + i];
+        const float rho = 1.0f + dr, ux = jx / rho, uy = jy / rho;
+        float n[FVLBM_Q];
+        float s = 0, sx = 0, sy = 0;
+#pragma unroll
+        for (int a = 3; a < FVLBM_Q; a++) {
+            n[a] = h2f<H>(h[(a - 3) * np + i]) * P.inv_scale[a];
+            s += n[a];
+            sx += float(EXA(a)) * n[a];
+            sy += float(EYA(a)) * n[a];
+        }
+        n[1] = -sx;
+        n[2] = -sy;
+        n[0] = -(s + n[1] + n[2]);
+#pragma unroll
+        for (int a = 0; a < FVLBM_Q; a++) f[a] = (T)(feqs<float, true>(a, dr, ux, uy) + n[a]);
     }
-    __device__ static void st(__nv_bfloat16* p, int64_t i, float v, float, float off) {
-        p[i] = __float2bfloat16_rn(v - off);
+    template <typename T, bool DEV>
+    __device__ static void store(void* base, int64_t i, int64_t np, const InstParam& P, const T* f) {
+        float* c = (float*)base;
+        H* h = (H*)(c + 3 * np);
+        float dr = 0, jx = 0, jy = 0;
+#pragma unroll
+        for (int a = 0; a < FVLBM_Q; a++) {
+            dr += (float)f[a];
+            jx += float(EXA(a)) * (float)f[a];
+            jy += float(EYA(a)) * (float)f[a];
+        }
+        c[i] = dr;
+        c[np + i] = jx;
+        c[2 * np + i] = jy;
+        const float rho = 1.0f + dr, ux = jx / rho, uy = jy / rho;
+#pragma unroll
+        for (int a = 3; a < FVLBM_Q; a++)
+            h[(a - 3) * np + i] = f2h<H>(((float)f[a] - feqs<float, true>(a, dr, ux, uy)) * P.scale[a]);
     }
+    __device__ static void moments64(const void* base, int64_t i, int64_t np, const InstParam&, double& r, double& jx,
+                                     double& jy) {
+        const float* c = (const float*)base;
+        r = c[i];
+        jx = c[np + i];
+        jy = c[2 * np + i];
+    }
+    static constexpr size_t bytes_per_cell = 3 * sizeof(float) + 6 * sizeof(H);
 };
+template <> struct CellIO<__half> : SplitIO<__half> {};
+template <> struct CellIO<__nv_bfloat16> : SplitIO<__nv_bfloat16> {};
 
 }  // namespace fvlbm

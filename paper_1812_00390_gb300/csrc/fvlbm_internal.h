@@ -66,9 +66,8 @@ struct Mesh {
 struct InstParam {
     double tau, inv_tau, dt;
     float inv_tau_f, dt_f;
-    float scale[FVLBM_Q];      // 16-bit storage: stored = (g - off) * scale
+    float scale[FVLBM_Q];      // 16-bit split storage: stored = (g_a - g^eq_a) * scale
     float inv_scale[FVLBM_Q];
-    float off[FVLBM_Q];        // 16-bit storage offset: f^eq(rho0, u0) - w
     double rho0, u0x, u0y;
 };
 

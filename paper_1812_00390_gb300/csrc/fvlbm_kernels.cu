@@ -36,9 +36,9 @@ __global__ void init_eq_kernel(DevView v) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.n_cell) return;
     const InstParam& P = v.inst[v.grp[i]];
-    S* f = (S*)v.fa;
-    for (int a = 0; a < FVLBM_Q; a++)
-        Store<S>::st(f, a * v.np + i, feqs<T, DEV>(a, rarg<T, DEV>(P.rho0), T(P.u0x), T(P.u0y)), P.scale[a], P.off[a]);
+    T f[FVLBM_Q];
+    for (int a = 0; a < FVLBM_Q; a++) f[a] = feqs<T, DEV>(a, rarg<T, DEV>(P.rho0), T(P.u0x), T(P.u0y));
+    CellIO<S>::template store<T, DEV>(v.fa, i, v.np, P, f);
 }
 
 // rho, u in FP64 from the stored state (Step 6).
@@ -46,15 +46,8 @@ template <typename T, typename S, bool DEV>
 __global__ void macros_kernel(DevView v) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.n_cell) return;
-    const InstParam& P = v.inst[v.grp[i]];
-    const S* f = (const S*)v.fa;
-    double r = 0, mx = 0, my = 0;
-    for (int a = 0; a < FVLBM_Q; a++) {
-        double x = (double)Store<S>::ld(f, a * v.np + i, P.inv_scale[a], P.off[a]);
-        r += x;
-        mx += EXA(a) * x;
-        my += EYA(a) * x;
-    }
+    double r, mx, my;
+    CellIO<S>::moments64(v.fa, i, v.np, v.inst[v.grp[i]], r, mx, my);
     double rho = DEV ? 1.0 + r : r;
     v.rho[i] = rho;
     v.ux[i] = mx / rho;
@@ -66,24 +59,21 @@ template <typename T, typename S, bool DEV>
 __global__ void get_f_kernel(DevView v) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.n_cell) return;
-    const InstParam& P = v.inst[v.grp[i]];
-    const S* f = (const S*)v.fa;
-    for (int a = 0; a < FVLBM_Q; a++) {
-        double x = (double)Store<S>::ld(f, a * v.np + i, P.inv_scale[a], P.off[a]);
-        v.conv[a * v.np + i] = DEV ? x + wgt<double>(a) : x;
-    }
+    T f[FVLBM_Q];
+    CellIO<S>::template load<T, DEV>(v.fa, i, v.np, v.inst[v.grp[i]], f);
+    for (int a = 0; a < FVLBM_Q; a++) v.conv[a * v.np + i] = DEV ? (double)f[a] + wgt<double>(a) : (double)f[a];
 }
 
 template <typename T, typename S, bool DEV>
 __global__ void set_f_kernel(DevView v) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.n_cell) return;
-    const InstParam& P = v.inst[v.grp[i]];
-    S* f = (S*)v.fa;
+    T f[FVLBM_Q];
     for (int a = 0; a < FVLBM_Q; a++) {
-        double x = v.conv[a * v.np + i];
-        Store<S>::st(f, a * v.np + i, (T)(DEV ? x - wgt<double>(a) : x), P.scale[a], P.off[a]);
+        const double x = v.conv[a * v.np + i];
+        f[a] = (T)(DEV ? x - wgt<double>(a) : x);
     }
+    CellIO<S>::template store<T, DEV>(v.fa, i, v.np, v.inst[v.grp[i]], f);
 }
 
 // Deterministic FP64 reductions: one block per chunk of one instance, fixed

@@ -53,12 +53,10 @@ __global__ void mass_chunks_static_kernel(DevView v, double* part) {
     __shared__ double sh[NA_THREADS];
     const int64_t ch = blockIdx.x;
     const int64_t b = v.chunk[3 * ch], e = v.chunk[3 * ch + 1];
-    const S* f = (const S*)v.fa;
     double s0 = 0;
     for (int64_t i = b + threadIdx.x; i < e; i += NA_THREADS) {
-        const InstParam& P = v.inst[v.grp[i]];
-        double r = 0;
-        for (int a = 0; a < FVLBM_Q; a++) r += (double)Store<S>::ld(f, a * v.np + i, P.inv_scale[a], P.off[a]);
+        double r, jx, jy;
+        CellIO<S>::moments64(v.fa, i, v.np, v.inst[v.grp[i]], r, jx, jy);
         const double rho = DEV ? 1.0 + r : r;
         s0 += v.area[i] * rho;
     }

@@ -73,8 +73,10 @@ constexpr size_t ALIGN = 256;
 constexpr int64_t CHUNK = 4096;
 
 size_t real_size(int prec) { return prec == FVLBM_FP64 ? 8 : 4; }
-size_t store_size(int prec) {
-    return prec == FVLBM_FP64 ? 8 : (prec == FVLBM_FP32_DEV ? 4 : 2);
+// bytes of stored state per cell: 9 values, or for the 16-bit split format
+// 3 FP32 moments + 6 16-bit non-equilibrium values
+size_t state_bytes(int prec) {
+    return prec == FVLBM_FP64 ? 72 : (prec == FVLBM_FP32_DEV ? 36 : 24);
 }
 
 // Halo structure of the fused stage kernel: tiles of `tile` consecutive cells
@@ -183,7 +185,7 @@ int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L) {
     L.maxf = M.max_faces <= 4 ? 4 : 8;
     L.n_chunk = 0;
     for (int k = 0; k < M.n_inst; k++) L.n_chunk += (M.inst_begin[k + 1] - M.inst_begin[k] + CHUNK - 1) / CHUNK;
-    const size_t R = real_size(prec), S = store_size(prec);
+    const size_t R = real_size(prec), S = state_bytes(prec);
     if (kernel != 0 && kernel != 1 && kernel != 128 && kernel != 256 && kernel != 512)
         return fail(FVLBM_ERR_ARG, "params.kernel = %d: use 0, 1, 128, 256 or 512", kernel);
     L.strategy = (kernel == 1 || (kernel == 0 && prec == FVLBM_FP64)) ? STRATEGY_TWO_KERNEL : STRATEGY_TILE;
@@ -222,8 +224,8 @@ int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L) {
     L.off_lnbr = take(tiled ? 2 * slots : 0);
     L.off_r1nbr = take(tiled ? 2 * L.tp.r1nbr.size() : 0);
     L.off_rn = take(tiled ? R * slots * 2 : 0);
-    L.off_fa = take(S * plane * FVLBM_Q);   // everything before this is uploaded once
-    L.off_fb = (scheme == FVLBM_RK2 || scheme == FVLBM_RK4) ? take(S * plane * FVLBM_Q) : 0;
+    L.off_fa = take(S * plane);   // everything before this is uploaded once
+    L.off_fb = (scheme == FVLBM_RK2 || scheme == FVLBM_RK4) ? take(S * plane) : 0;
     L.off_rprev = scheme == FVLBM_AB2 ? take(R * plane * FVLBM_Q) : 0;
     L.off_fv = take(two ? R * (size_t)std::max<int64_t>(1, L.n_face) * (FVLBM_Q - 1) : 0);
     L.off_rho = take(8 * plane);
@@ -390,17 +392,12 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
         I.u0x = p.u0[0];
         I.u0y = p.u0[1];
         for (int a = 0; a < FVLBM_Q; a++) {
-            const double w = a == 0 ? 4.0 / 9 : (a < 5 ? 1.0 / 9 : 1.0 / 36);
-            const double ex = a == 1 || a == 5 || a == 8 ? 1 : (a == 3 || a == 6 || a == 7 ? -1 : 0);
-            const double ey = a == 2 || a == 5 || a == 6 ? 1 : (a == 4 || a == 7 || a == 8 ? -1 : 0);
-            float sc = 1.0f, off = 0.0f;
-            if (p.precision == FVLBM_FP16_DEV || p.precision == FVLBM_BF16_DEV) {
-                // offset: deviation of the initial equilibrium f^eq(rho0, u0) - w (Eq. feq)
-                const double eu = ex * p.u0[0] + ey * p.u0[1], uu = p.u0[0] * p.u0[0] + p.u0[1] * p.u0[1];
-                off = (float)(w * ((p.rho0 - 1.0) + p.rho0 * (3 * eu + 4.5 * eu * eu - 1.5 * uu)));
-            }
+            float sc = 1.0f;
             if (p.precision == FVLBM_FP16_DEV) {
-                // power-of-two scale mapping a bound of |g - off| to ~2^12
+                // power-of-two scale of the stored non-equilibrium part: a bound
+                // of |g_a - g^eq_a| (at most the size of the equilibrium
+                // deviation itself) maps to ~2^12, far inside FP16's range
+                const double w = a == 0 ? 4.0 / 9 : (a < 5 ? 1.0 / 9 : 1.0 / 36);
                 const double e = a == 0 ? 0.0 : (a < 5 ? 1.0 : std::sqrt(2.0));
                 const double U = std::max(umax, 1e-3);
                 const double gmax = w * (0.1 + 2.2 * (3 * e * U + 4.5 * e * e * U * U + 1.5 * U * U));
@@ -408,7 +405,6 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
             }
             I.scale[a] = sc;
             I.inv_scale[a] = 1.0f / sc;
-            I.off[a] = off;
         }
     }
 

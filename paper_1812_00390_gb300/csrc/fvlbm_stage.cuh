@@ -15,39 +15,6 @@ template <> __device__ __forceinline__ double inst_inv_tau<double>(const InstPar
 template <> __device__ __forceinline__ float inst_inv_tau<float>(const InstParam& p) { return p.inv_tau_f; }
 
 // ------------------------------------------------------------------ physics
-// Density and velocity (Sec. 2.1).  FP64 mode: r = rho = sum f.  Deviation
-// mode: r = rho - 1 = sum g, kept unrounded by the 1 so that the density
-// deviation keeps FP32 relative precision.
-template <typename T, bool DEV>
-__device__ __forceinline__ void moments(const T* f, T& r, T& ux, T& uy) {
-    T s = 0, mx = 0, my = 0;
-#pragma unroll
-    for (int a = 0; a < FVLBM_Q; a++) {
-        s += f[a];
-        mx += T(EXA(a)) * f[a];
-        my += T(EYA(a)) * f[a];
-    }
-    r = s;
-    const T rho = DEV ? T(1) + s : s;
-    ux = mx / rho;
-    uy = my / rho;
-}
-
-// Eq. (feq).  FP64 mode: r = rho, returns f^eq.  Deviation mode: r = rho - 1,
-// returns f^eq - w = w [(rho - 1) + rho (3 e.u + 4.5 (e.u)^2 - 1.5 u^2)].
-template <typename T, bool DEV>
-__device__ __forceinline__ T feqs(int a, T r, T ux, T uy) {
-    T eu = T(EXA(a)) * ux + T(EYA(a)) * uy;
-    T uu = ux * ux + uy * uy;
-    T poly = T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu;
-    if (DEV) return wgt<T>(a) * (r + (T(1) + r) * poly);
-    return r * wgt<T>(a) * (T(1) + poly);
-}
-
-// Density argument of feqs for a given density.
-template <typename T, bool DEV>
-__device__ __forceinline__ T rarg(double rho) { return DEV ? T(rho - 1.0) : T(rho); }
-
 // Stencil value minus the cell value for a boundary slot (Sec. 2.4.1):
 //   wall      f^eq(rho, u_w) - f^eq(rho, u)                        Eq. (wallbc)
 //   inlet     f^eq(rho*, u_inf) - f^eq(rho, u), rho* = rho_inf or rho
@@ -83,8 +50,7 @@ __global__ void __launch_bounds__(256) face_values_kernel(DevView v, const S* __
     T* fv = (T*)v.fv;
 
     T f[FVLBM_Q];
-#pragma unroll
-    for (int a = 0; a < FVLBM_Q; a++) f[a] = Store<S>::ld(fin, a * np + i, P.inv_scale[a], P.off[a]);
+    CellIO<S>::template load<T, DEV>(fin, i, np, P, f);
     T rho, ux, uy;
     moments<T, DEV>(f, rho, ux, uy);
 
@@ -100,9 +66,11 @@ __global__ void __launch_bounds__(256) face_values_kernel(DevView v, const S* __
         const T cx = cg[(0 * MAXF + k) * np + i], cy = cg[(1 * MAXF + k) * np + i];
         if (kind == SK_INTERIOR) {
             const int64_t j = v.nbr[k * np + i];
+            T fj[FVLBM_Q];
+            CellIO<S>::template load<T, DEV>(fin, j, np, v.inst[v.grp[j]], fj);
 #pragma unroll
             for (int a = 1; a < FVLBM_Q; a++) {
-                T d = Store<S>::ld(fin, a * np + j, P.inv_scale[a], P.off[a]) - f[a];
+                T d = fj[a] - f[a];
                 gx[a - 1] += cx * d;
                 gy[a - 1] += cy * d;
             }
@@ -165,8 +133,7 @@ __global__ void __launch_bounds__(256) update_kernel(DevView v, const S* __restr
     const T* fv = (const T*)v.fv;
 
     T f[FVLBM_Q];
-#pragma unroll
-    for (int a = 0; a < FVLBM_Q; a++) f[a] = Store<S>::ld(fin, a * np + i, P.inv_scale[a], P.off[a]);
+    CellIO<S>::template load<T, DEV>(fin, i, np, P, f);
     T rho, ux, uy;
     moments<T, DEV>(f, rho, ux, uy);
 
@@ -194,23 +161,23 @@ __global__ void __launch_bounds__(256) update_kernel(DevView v, const S* __restr
     const T dt = inst_dt<T>(P);
     bool bad = false;
     T* rp = (T*)v.rprev;
+    T fb[FVLBM_Q], out[FVLBM_Q];
+    if (mode == MODE_RK && fbase != fin) CellIO<S>::template load<T, DEV>(fbase, i, np, P, fb);
 #pragma unroll
     for (int a = 0; a < FVLBM_Q; a++) {
         const T rhs = -flux[a] - (f[a] - feqs<T, DEV>(a, rho, ux, uy)) * inv_tau;
-        T out;
         if (mode == MODE_RK) {
-            const T base = (fbase == fin) ? f[a] : Store<S>::ld(fbase, a * np + i, P.inv_scale[a], P.off[a]);
-            out = base + beta * dt * rhs;
+            out[a] = (fbase == fin ? f[a] : fb[a]) + beta * dt * rhs;
         } else if (mode == MODE_AB2_FIRST) {
-            out = f[a] + dt * rhs;
+            out[a] = f[a] + dt * rhs;
             rp[a * np + i] = rhs;
         } else {
-            out = f[a] + dt * (T(1.5) * rhs - T(0.5) * rp[a * np + i]);
+            out[a] = f[a] + dt * (T(1.5) * rhs - T(0.5) * rp[a * np + i]);
             rp[a * np + i] = rhs;
         }
-        bad |= !finite_val(out);
-        Store<S>::st(fout, a * np + i, out, P.scale[a], P.off[a]);
+        bad |= !finite_val(out[a]);
     }
+    CellIO<S>::template store<T, DEV>(fout, i, np, P, out);
     if (bad) *v.flag = 1;
 }
 
@@ -247,9 +214,10 @@ __global__ void __launch_bounds__(TILE) stage_tile_kernel(DevView v, const S* __
     // phase 1
     for (int l = threadIdx.x; l < nl; l += TILE) {
         const int64_t gi = l < nt ? c0 + l : (int64_t)v.halo[h0 + l - nt];
-        const InstParam& P = v.inst[v.grp[gi]];
+        T f[FVLBM_Q];
+        CellIO<S>::template load<T, DEV>(fin, gi, np, v.inst[v.grp[gi]], f);
 #pragma unroll
-        for (int a = 0; a < FVLBM_Q; a++) fs[a * lmax + l] = Store<S>::ld(fin, a * np + gi, P.inv_scale[a], P.off[a]);
+        for (int a = 0; a < FVLBM_Q; a++) fs[a * lmax + l] = f[a];
     }
     __syncthreads();
 
@@ -359,23 +327,23 @@ __global__ void __launch_bounds__(TILE) stage_tile_kernel(DevView v, const S* __
     const T dt = inst_dt<T>(P);
     bool bad = false;
     T* rp = (T*)v.rprev;
+    T fb[FVLBM_Q], outv[FVLBM_Q];
+    if (mode == MODE_RK && fbase != fin) CellIO<S>::template load<T, DEV>(fbase, gi, np, P, fb);
 #pragma unroll
     for (int a = 0; a < FVLBM_Q; a++) {
         const T rhs = -flux[a] - (f[a] - feqs<T, DEV>(a, rho, ux, uy)) * inv_tau;
-        T outv;
         if (mode == MODE_RK) {
-            const T base = (fbase == fin) ? f[a] : Store<S>::ld(fbase, a * np + gi, P.inv_scale[a], P.off[a]);
-            outv = base + beta * dt * rhs;
+            outv[a] = (fbase == fin ? f[a] : fb[a]) + beta * dt * rhs;
         } else if (mode == MODE_AB2_FIRST) {
-            outv = f[a] + dt * rhs;
+            outv[a] = f[a] + dt * rhs;
             rp[a * np + gi] = rhs;
         } else {
-            outv = f[a] + dt * (T(1.5) * rhs - T(0.5) * rp[a * np + gi]);
+            outv[a] = f[a] + dt * (T(1.5) * rhs - T(0.5) * rp[a * np + gi]);
             rp[a * np + gi] = rhs;
         }
-        bad |= !finite_val(outv);
-        Store<S>::st(fout, a * np + gi, outv, P.scale[a], P.off[a]);
+        bad |= !finite_val(outv[a]);
     }
+    CellIO<S>::template store<T, DEV>(fout, gi, np, P, outv);
     if (bad) *v.flag = 1;
 }
 

@@ -217,25 +217,31 @@ def test_batch_equals_solo(fv, orc):
             off += m.n_cell
 
 
-def test_cavity_fp32_velocity_error(fv, orc):
-    """Lid-driven cavity 128^2 (tanh-stretched, 1:20), Re = 400, RK2, 10^4 steps:
-    FP32 deviation mode against the FP64 oracle, relative velocity error <= 1e-5."""
+def test_cavity_mixed_precision_velocity_error(fv, orc):
+    """Lid-driven cavity 128^2 (tanh-stretched, 1:20), Re = 400, RK2, 10^4 steps
+    against the FP64 oracle: FP32 deviation mode within 1e-5 relative velocity
+    error; the 16-bit split formats (FP32 rho, rho u; 16-bit non-equilibrium
+    part) within the bounds stated for them."""
     m = mg.cavity(128, 20.0, U=0.1)
     tau = 3 * 0.1 / 400
     o = orc.Oracle(m)
     dt = o.cfl_dt(0.5, 0.1, tau, "rk2")
-    s = fv.Solver(fv.Mesh(m), fv.make_params(tau, dt=dt, scheme="rk2", precision="fp32"))
     n = 10000
-    s.step(n)
+    sol = {p: fv.Solver(fv.Mesh(m), fv.make_params(tau, dt=dt, scheme="rk2", precision=p))
+           for p in ("fp32", "fp16", "bf16")}
+    for s in sol.values():
+        s.step(n)
     o.set_equilibrium(1.0, (0.0, 0.0))
     o.run("rk2", tau, dt, n)
-    _, ug = s.macros()
     _, uo = o.macros()
-    err = np.abs(ug - uo).max() / np.abs(uo).max()
-    assert err < 1e-5, err
+    err = {p: np.abs(s.macros()[1] - uo).max() / np.abs(uo).max() for p, s in sol.items()}
+    print("cavity relative velocity error after 1e4 steps:", err)
+    assert err["fp32"] < 1e-5, err
+    assert err["fp16"] < 1e-4, err
+    assert err["bf16"] < 1e-3, err
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32", 5e-6), ("fp16", 1e-2), ("bf16", 0.2)])
+@pytest.mark.parametrize("prec,tol", [("fp32", 5e-6), ("fp16", 5e-5), ("bf16", 5e-4)])
 def test_deviation_modes_error_bound(fv, orc, prec, tol):
     """Stored-precision error after 500 RK2 steps of a cylinder hybrid mesh (far
     field, wall), relative to the largest velocity."""
