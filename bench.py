@@ -328,7 +328,9 @@ def run_ours(args):
     # FP64 on the same workload, and the mixed-mode error against it
     ms64 = None
     err = None
+    fp64_peak = None
     if not args.no_fp64:
+        fp64_peak = fv.fma_peak(dev, fp64=True)
         k64 = max(3, args.steps // 8)
         kernel64, tune64 = tune_kernel(fv, handles, inst, "fp64")
         s64, _ = build_solver(fv, variants, inst, "fp64", handles=handles, kernel=kernel64)
@@ -347,6 +349,23 @@ def run_ours(args):
         ref32.close()
         err = float(np.abs(u32 - u64).max() / np.abs(u64).max())
         err_steps = n_cmp
+
+    # FP16 split storage (FP32 rho, rho u; 16-bit non-equilibrium part) on the same workload
+    fp16 = None
+    if not args.no_fp16:
+        s16, _ = build_solver(fv, variants, inst, "fp16", handles=handles, kernel=kernel32)
+        ms16, _ = timed(s16, max(3, args.steps // 4))
+        ms16 /= max(3, args.steps // 4)
+        fp16 = {"value": n_cells * world / (ms16 / 1e3) / 1e6, "unit": "MCUPS", "ms_per_step": ms16,
+                "storage": "rho-1, rho u in FP32 + 6 non-equilibrium components in FP16 (24 B/cell)"}
+        if err is not None:
+            s16.close()
+            s16, _ = build_solver(fv, variants, inst, "fp16", handles=handles, kernel=kernel32)
+            s16.step(err_steps)
+            _, u16 = s16.macros()
+            fp16["max_rel_velocity_error_vs_fp64"] = float(np.abs(u16 - u64).max() / np.abs(u64).max())
+            fp16["steps"] = err_steps
+        s16.close()
 
     # roofline of the stage kernels: algorithmic f traffic per RK2 stage,
     # stage 1 reads f0 and writes f1, stage 2 reads f1 and f0 and writes f
@@ -414,7 +433,10 @@ def run_ours(args):
                        "stage_kernel": kernel32,
                        "autotune_ms_per_step": {str(k): v for k, v in tune32.items()}},
             "fp64": {"value": (n_cells * world / (ms64 / 1e3) / 1e6) if ms64 else None, "unit": "MCUPS",
-                     "ms_per_step": ms64, "stage_kernel": kernel64 if ms64 else None},
+                     "ms_per_step": ms64, "stage_kernel": kernel64 if ms64 else None,
+                     "fma_peak_tflops": fp64_peak,
+                     "note": "FP64 stage is bound by the FP64 units, not HBM"},
+            "fp16_split": fp16,
             "mixed_over_fp64": (value / (n_cells * world / (ms64 / 1e3) / 1e6)) if ms64 else None,
             "mixed_error_vs_fp64": ({"max_rel_velocity": err, "steps": err_steps} if err is not None else None),
             "roofline": roof,
@@ -450,6 +472,7 @@ def main():
     ap.add_argument("--serving-arena-gb", type=float, default=8.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-fp16", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -278,6 +278,13 @@ int fvlbm_profile(fvlbm_solver* s, int64_t n, double* avg_ms, int32_t max_kinds,
 int fvlbm_autotune(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t n_params, void* stream,
                    int32_t steps, int32_t* best_kernel, double* ms_per_step);
 
+/*
+ * Measurement aid: sustained FMA rate of the device, in TFLOP/s (2 flop per
+ * FMA), from dependent FMA chains on every SM; fp64 != 0 for FP64, else FP32.
+ * Allocates and frees a small buffer.  tflops: host, written.
+ */
+int fvlbm_fma_peak(int32_t device, int32_t fp64, double* tflops);
+
 /* Kernels one time step launches (host, written). */
 int fvlbm_launches_per_step(const fvlbm_solver* s, int64_t* launches);
 

@@ -173,3 +173,62 @@ int launch_reduce(const DevView& v, void* stream, int what) {
 }
 
 }  // namespace fvlbm
+
+// ------------------------------------------------------------------ FMA peak
+// Dependent FMA chains, 8 per thread, enough warps to fill every SM: the
+// sustained FMA rate of the device in FP64 or FP32 (2 flop per FMA).
+namespace fvlbm {
+template <typename T>
+__global__ void fma_peak_kernel(T* out, int iters, T a, T b) {
+    T x[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) x[k] = (T)(threadIdx.x + k);
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int k = 0; k < 8; k++) x[k] = x[k] * a + b;
+    }
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) s += x[k];
+    if (s == (T)-1) out[blockIdx.x * blockDim.x + threadIdx.x] = s;   // keeps the chains live
+}
+}  // namespace fvlbm
+
+extern "C" int fvlbm_fma_peak(int32_t device, int32_t fp64, double* tflops) {
+    using namespace fvlbm;
+    clear_error();
+    if (!tflops) return fail(FVLBM_ERR_ARG, "fvlbm_fma_peak: null output");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(device) != cudaSuccess) return fail(FVLBM_ERR_UNSUPPORTED, "no CUDA device %d", device);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const int threads = 256, blocks = sms * 8, iters = fp64 ? 2048 : 16384;
+    void* out = nullptr;
+    cudaEvent_t e0, e1;
+    int rc = FVLBM_OK;
+    if (cudaMalloc(&out, sizeof(double) * threads * blocks) != cudaSuccess) rc = fail(FVLBM_ERR_OOM, "fma peak buffer");
+    if (!rc) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        for (int rep = 0; rep < 4; rep++) {
+            cudaEventRecord(e0);
+            if (fp64) fma_peak_kernel<double><<<blocks, threads>>>((double*)out, iters, 0.999999, 1e-7);
+            else fma_peak_kernel<float><<<blocks, threads>>>((float*)out, iters, 0.999999f, 1e-7f);
+            cudaEventRecord(e1);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && ms < best) best = ms;
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = fail(FVLBM_ERR_CUDA, "fma peak: %s", cudaGetErrorString(e));
+        else *tflops = 2.0 * 8.0 * iters * (double)threads * blocks / (best * 1e-3) / 1e12;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaFree(out);
+    }
+    if (prev >= 0) cudaSetDevice(prev);
+    return rc;
+}

@@ -73,7 +73,7 @@ class ServerStatsT(C.Structure):
 EXPORTS = ["fvlbm_mesh_create", "fvlbm_mesh_concat", "fvlbm_mesh_destroy", "fvlbm_mesh_info",
            "fvlbm_suggest_dt", "fvlbm_workspace_bytes", "fvlbm_init", "fvlbm_step", "fvlbm_macros",
            "fvlbm_residual", "fvlbm_mass", "fvlbm_mass_noalloc", "fvlbm_get_f", "fvlbm_set_f", "fvlbm_sync",
-           "fvlbm_get_dt", "fvlbm_profile", "fvlbm_autotune", "fvlbm_launches_per_step", "fvlbm_solver_destroy",
+           "fvlbm_get_dt", "fvlbm_profile", "fvlbm_autotune", "fvlbm_fma_peak", "fvlbm_launches_per_step", "fvlbm_solver_destroy",
            "fvlbm_server_create", "fvlbm_server_submit", "fvlbm_server_poll", "fvlbm_server_request",
            "fvlbm_server_stats", "fvlbm_server_destroy", "fvlbm_last_error"]
 
@@ -109,6 +109,7 @@ def _load():
         "fvlbm_profile": [P, C.c_int64, dp, C.c_int32, i32p, i64p],
         "fvlbm_launches_per_step": [P, i64p],
         "fvlbm_autotune": [P, C.POINTER(ParamsT), C.c_int32, P, C.c_int32, i32p, dp],
+        "fvlbm_fma_peak": [C.c_int32, C.c_int32, dp],
         "fvlbm_solver_destroy": [P],
         "fvlbm_server_create": [C.POINTER(ServerConfigT), PP],
         "fvlbm_server_submit": [P, P, C.POINTER(ParamsT), C.c_int32, i64p],
@@ -323,6 +324,13 @@ class Solver:
 
 
 KERNEL_VARIANTS = (1, 128, 256, 512)
+
+
+def fma_peak(device: int = 0, fp64: bool = True) -> float:
+    """Sustained FMA throughput of the device in TFLOP/s (FP64 or FP32)."""
+    t = C.c_double()
+    _check(lib.fvlbm_fma_peak(device, 1 if fp64 else 0, C.byref(t)))
+    return t.value
 
 
 def autotune(mesh: Mesh, params, steps: int = 10, stream=None):
