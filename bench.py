@@ -85,7 +85,7 @@ def build_solver(fv, variants, inst, precision, scheme="rk2", handles=None, kern
     return fv.Solver(mesh, params), handles
 
 
-def tune_kernel(fv, handles, inst, precision, scheme="rk2", n_sample=12, steps=10):
+def tune_kernel(fv, handles, inst, precision, scheme="rk2", n_sample=24, steps=20):
     """Stage-kernel variant chosen by the library's autotuner on the first
     n_sample instances of the batch (all three kinds)."""
     sub = inst[:n_sample]
@@ -292,7 +292,10 @@ def run_ours(args):
         cpu = {"value": v, "unit": "MCUPS", "cores": thr, "kind": "oracle", "sample": sample}
 
     handles = {k: fv.Mesh(m) for k, m in variants.items()}
-    kernel32, tune32 = tune_kernel(fv, handles, inst, "fp32")
+    if args.kernel is not None:
+        kernel32, tune32 = args.kernel, {}
+    else:
+        kernel32, tune32 = tune_kernel(fv, handles, inst, "fp32")
     s32, _ = build_solver(fv, variants, inst, "fp32", handles=handles, kernel=kernel32)
     n_cells = s32.n_cell
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -332,7 +335,10 @@ def run_ours(args):
     if not args.no_fp64:
         fp64_peak = fv.fma_peak(dev, fp64=True)
         k64 = max(3, args.steps // 8)
-        kernel64, tune64 = tune_kernel(fv, handles, inst, "fp64")
+        if args.kernel is not None:
+            kernel64, tune64 = args.kernel, {}
+        else:
+            kernel64, tune64 = tune_kernel(fv, handles, inst, "fp64")
         s64, _ = build_solver(fv, variants, inst, "fp64", handles=handles, kernel=kernel64)
         ms64, _ = timed(s64, k64)
         ms64 /= k64
@@ -473,6 +479,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-fp16", action="store_true")
+    ap.add_argument("--kernel", type=int, default=None,
+                    help="stage kernel variant (1, 128, 256, 512) instead of the autotuner's choice")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
