@@ -94,6 +94,48 @@ def tune_kernel(fv, handles, inst, precision, scheme="rk2", n_sample=24, steps=2
     return fv.autotune(mesh, params, steps=steps)
 
 
+# ----------------------------------------------------------------------------- single configs
+def config_runs(fv, torch, dev, steps: int = 30):
+    """MCUPS of the single-mesh configurations.  Their state fits in L2, so every
+    timed step is preceded by writing a 256 MB buffer (L2 flush) outside the
+    timed events ("cold"); "warm" is the same solver replaying its graphs with
+    the mesh resident in L2."""
+    from paper_1812_00390_gb300 import meshgen as mg
+    cases = [
+        ("couette_32x8_euler_fp64", mg.couette(), 3 * 0.1 * 8 / 10, "euler", "fp64", (0.0, 0.0)),
+        ("cavity_128_re400_rk2_fp32", mg.cavity(128, 20.0), 3 * 0.1 / 400, "rk2", "fp32", (0.0, 0.0)),
+        ("cavity_128_re400_rk2_fp64", mg.cavity(128, 20.0), 3 * 0.1 / 400, "rk2", "fp64", (0.0, 0.0)),
+        ("cylinder_60k_re40_rk2_fp16split", mg.cylinder_hybrid(), 3 * 0.05 / 40, "rk2", "fp16", (0.05, 0.0)),
+        ("cylinder_60k_re40_rk2_fp32", mg.cylinder_hybrid(), 3 * 0.05 / 40, "rk2", "fp32", (0.05, 0.0)),
+    ]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
+    out = {}
+    for name, m, tau, scheme, prec, u0 in cases:
+        s = fv.Solver(fv.Mesh(m), fv.make_params(tau, scheme=scheme, precision=prec, u0=u0))
+        s.step(5)
+        s.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush.fill_(1)
+            torch.cuda.current_stream(dev).synchronize()
+            a.record(s.stream)
+            s.step(1)
+            b.record(s.stream)
+        s.sync()
+        cold = sum(a.elapsed_time(b) for a, b in ev) / steps
+        a, b = ev[0]
+        a.record(s.stream)
+        s.step(10 * steps)
+        b.record(s.stream)
+        s.sync()
+        warm = a.elapsed_time(b) / (10 * steps)
+        out[name] = {"cells": m.n_cell, "cold_l2_mcups": m.n_cell / (cold / 1e3) / 1e6,
+                     "warm_l2_mcups": m.n_cell / (warm / 1e3) / 1e6, "cold_ms_per_step": cold,
+                     "warm_ms_per_step": warm}
+        s.close()
+    return out
+
+
 # ----------------------------------------------------------------------------- ranks
 def reduce_max(x: float, dist, device=None) -> float:
     """Largest value over all ranks (the slowest rank's time); x itself at N = 1."""
@@ -409,6 +451,8 @@ def run_ours(args):
         e2e_s = time.perf_counter() - t0
         e2e_val = n_cells * world * e2e_inner * args.e2e_steps / e2e_s / 1e6
 
+    configs = config_runs(fv, torch, dev) if (args.configs and rank == 0) else None
+
     # serving stream (config 5): Poisson arrivals of tandem / single cylinder
     # solves on the continuous-batching server, p50 / p99 time to completion
     serving = None
@@ -452,6 +496,7 @@ def run_ours(args):
                      "definition": f"set_f from host + {e2e_inner} time steps + residual read-back"}
                     if e2e_val is not None else None),
             "serving": serving,
+            "single_configs": configs,
             "gpu_launches": launches,
             "clocks": clocks,
         }
@@ -476,11 +521,13 @@ def main():
     ap.add_argument("--serving-rate", type=float, default=2.0, help="Poisson arrivals per second")
     ap.add_argument("--serving-steps", type=int, default=20000)
     ap.add_argument("--serving-arena-gb", type=float, default=8.0)
+    ap.add_argument("--no-configs", dest="configs", action="store_false",
+                    help="skip the single-mesh configurations")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-fp16", action="store_true")
     ap.add_argument("--kernel", type=int, default=None,
-                    help="stage kernel variant (1, 128, 256, 512) instead of the autotuner's choice")
+                    help="stage kernel variant (1, 128, 256, 512, 1024) instead of the autotuner's choice")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -106,8 +106,8 @@ typedef struct fvlbm_params {
     double u0[2];      /* initial velocity */
     int32_t device;    /* CUDA device ordinal; equal for all instances */
     int32_t kernel;    /* stage kernel: 0 = automatic; 1 = two kernels per stage (face
-                          values through memory); 128, 256 or 512 = one fused kernel per
-                          stage with that many cells per tile; equal for all instances */
+                          values through memory); 128, 256, 512 or 1024 = one fused kernel
+                          per stage with that many cells per tile; equal for all instances */
 } fvlbm_params;
 
 typedef struct fvlbm_mesh_info_s {
@@ -266,12 +266,12 @@ int fvlbm_profile(fvlbm_solver* s, int64_t n, double* avg_ms, int32_t max_kinds,
 
 /*
  * Autotuner: time every stage-kernel variant (params.kernel = 1, 128, 256,
- * 512; variants that do not fit are skipped) on this mesh and parameters for
+ * 512, 1024; variants that do not fit are skipped) on this mesh and parameters for
  * `steps` steps after 2 warm-up steps, each in a temporary solver whose
  * workspace the library allocates and frees, and report the fastest.
  *   stream       as for fvlbm_init
  *   best_kernel  host, written: the value to put in fvlbm_params.kernel
- *   ms_per_step  host [4] or NULL: device ms per step of each variant in the
+ *   ms_per_step  host [5] or NULL: device ms per step of each variant in the
  *                order above (+inf when skipped)
  * Errors: FVLBM_ERR_ARG, _CUDA, _UNSUPPORTED (no variant fits).
  */

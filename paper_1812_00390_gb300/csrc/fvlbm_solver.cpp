@@ -174,10 +174,10 @@ struct Layout {
 };
 
 constexpr size_t SMEM_LIMIT = 227 * 1024;
-constexpr int64_t PLANE_ALIGN = 512;   // planes hold whole tiles of the largest tile size
+constexpr int64_t PLANE_ALIGN = 1024;  // planes hold whole tiles of the largest tile size
 
 // kernel: 0 automatic (fused tile 256, except FP64: two kernels, which spend
-// fewer FP64 operations), 1 two-kernel, 128/256/512 fused with that tile size.
+// fewer FP64 operations), 1 two-kernel, 128/256/512/1024 fused with that tile size.
 int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L) {
     L = Layout{};
     L.np = (M.n_cell + PLANE_ALIGN - 1) / PLANE_ALIGN * PLANE_ALIGN;
@@ -186,8 +186,8 @@ int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L) {
     L.n_chunk = 0;
     for (int k = 0; k < M.n_inst; k++) L.n_chunk += (M.inst_begin[k + 1] - M.inst_begin[k] + CHUNK - 1) / CHUNK;
     const size_t R = real_size(prec), S = state_bytes(prec);
-    if (kernel != 0 && kernel != 1 && kernel != 128 && kernel != 256 && kernel != 512)
-        return fail(FVLBM_ERR_ARG, "params.kernel = %d: use 0, 1, 128, 256 or 512", kernel);
+    if (kernel != 0 && kernel != 1 && kernel != 128 && kernel != 256 && kernel != 512 && kernel != 1024)
+        return fail(FVLBM_ERR_ARG, "params.kernel = %d: use 0, 1, 128, 256, 512 or 1024", kernel);
     L.strategy = (kernel == 1 || (kernel == 0 && prec == FVLBM_FP64)) ? STRATEGY_TWO_KERNEL : STRATEGY_TILE;
     if (L.strategy == STRATEGY_TILE) {
         make_tiles(M, L.np, L.maxf, kernel == 0 ? 256 : kernel, L.tp);
@@ -843,11 +843,11 @@ extern "C" int fvlbm_autotune(const fvlbm_mesh* mesh, const fvlbm_params* params
     clear_error();
     if (!mesh || !params || n_params <= 0 || steps <= 0 || !best_kernel)
         return fail(FVLBM_ERR_ARG, "fvlbm_autotune: bad arguments");
-    static const int32_t cand[4] = {1, 128, 256, 512};
+    static const int32_t cand[5] = {1, 128, 256, 512, 1024};
     std::vector<fvlbm_params> p(params, params + n_params);
     double best = INFINITY;
     int32_t pick = 0;
-    for (int c = 0; c < 4; c++) {
+    for (int c = 0; c < 5; c++) {
         if (ms_per_step) ms_per_step[c] = INFINITY;
         for (auto& q : p) q.kernel = cand[c];
         fvlbm_solver* sv = nullptr;

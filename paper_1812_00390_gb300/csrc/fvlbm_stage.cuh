@@ -376,6 +376,7 @@ static int tile_dispatch(const DevView& v, cudaStream_t st, const void* fin, con
         case 128: return tile_launch<T, S, MAXF, DEV, 128>(v, st, fin, fbase, fout, beta, mode);
         case 256: return tile_launch<T, S, MAXF, DEV, 256>(v, st, fin, fbase, fout, beta, mode);
         case 512: return tile_launch<T, S, MAXF, DEV, 512>(v, st, fin, fbase, fout, beta, mode);
+        case 1024: return tile_launch<T, S, MAXF, DEV, 1024>(v, st, fin, fbase, fout, beta, mode);
     }
     return fail(FVLBM_ERR_ARG, "unsupported tile size %d", v.tile);
 }

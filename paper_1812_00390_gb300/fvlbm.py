@@ -323,7 +323,7 @@ class Solver:
         self.close()
 
 
-KERNEL_VARIANTS = (1, 128, 256, 512)
+KERNEL_VARIANTS = (1, 128, 256, 512, 1024)
 
 
 def fma_peak(device: int = 0, fp64: bool = True) -> float:
@@ -342,7 +342,7 @@ def autotune(mesh: Mesh, params, steps: int = 10, stream=None):
         stream = torch.cuda.Stream(device=plist[0].device)
     sh = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
     best = C.c_int32()
-    ms = np.zeros(4)
+    ms = np.zeros(5)
     _check(lib.fvlbm_autotune(mesh._h, arr, len(plist), C.c_void_p(sh), steps, C.byref(best), _d(ms)))
     return best.value, dict(zip(KERNEL_VARIANTS, ms.tolist()))
 

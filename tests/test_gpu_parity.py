@@ -86,7 +86,7 @@ def test_fp64_parity_every_mesh_and_scheme(fv, orc, name, scheme):
     s.close()
 
 
-@pytest.mark.parametrize("kernel", [1, 128, 256, 512])
+@pytest.mark.parametrize("kernel", [1, 128, 256, 512, 1024])
 @pytest.mark.parametrize("name", ["cylinder", "bricks", "internal_io", "two_tri_periodic", "cavity_tri"])
 def test_stage_kernel_variants(fv, orc, name, kernel):
     """Two-kernel stage and fused stage (each tile size) against the oracle in
