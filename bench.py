@@ -111,7 +111,9 @@ def config_runs(fv, torch, dev, steps: int = 30):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
     out = {}
     for name, m, tau, scheme, prec, u0 in cases:
-        s = fv.Solver(fv.Mesh(m), fv.make_params(tau, scheme=scheme, precision=prec, u0=u0))
+        h = fv.Mesh(m)
+        best, _ = fv.autotune(h, fv.make_params(tau, scheme=scheme, precision=prec, u0=u0), steps=20)
+        s = fv.Solver(h, fv.make_params(tau, scheme=scheme, precision=prec, u0=u0, kernel=best))
         s.step(5)
         s.sync()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -129,7 +131,7 @@ def config_runs(fv, torch, dev, steps: int = 30):
         b.record(s.stream)
         s.sync()
         warm = a.elapsed_time(b) / (10 * steps)
-        out[name] = {"cells": m.n_cell, "cold_l2_mcups": m.n_cell / (cold / 1e3) / 1e6,
+        out[name] = {"cells": m.n_cell, "stage_kernel": best, "cold_l2_mcups": m.n_cell / (cold / 1e3) / 1e6,
                      "warm_l2_mcups": m.n_cell / (warm / 1e3) / 1e6, "cold_ms_per_step": cold,
                      "warm_ms_per_step": warm}
         s.close()

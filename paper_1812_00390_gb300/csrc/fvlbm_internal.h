@@ -114,6 +114,7 @@ struct DevView {
     int32_t* flag;  // non-finite flag
     // fused stage (one CTA per tile of `tile` consecutive cells)
     int32_t strategy;        // STRATEGY_TWO_KERNEL or STRATEGY_TILE
+    int32_t block;           // threads per block of the two-kernel stage
     int32_t tile;            // cells per tile (threads per CTA)
     int64_t n_tiles;
     int32_t lmax;            // most local cells (tile + halo) of any tile

@@ -167,6 +167,7 @@ struct Layout {
     int64_t np, n_face, n_chunk;
     int maxf;
     int strategy;
+    int block;
     TilePlan tp;
     size_t off_nbr, off_fid, off_meta, off_cg, off_rv, off_nv, off_area, off_grp, off_inst, off_bc,
         off_fa, off_fb, off_rprev, off_fv, off_rho, off_ux, off_uy, off_uold, off_part, off_red, off_conv,
@@ -174,11 +175,25 @@ struct Layout {
 };
 
 constexpr size_t SMEM_LIMIT = 227 * 1024;
+
+// Streaming multiprocessors of a device (152 on GB300 when no device answers).
+int device_sms(int device) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        n = 152;
+    }
+    return n;
+}
 constexpr int64_t PLANE_ALIGN = 1024;  // planes hold whole tiles of the largest tile size
 
-// kernel: 0 automatic (fused tile 256, except FP64: two kernels, which spend
-// fewer FP64 operations), 1 two-kernel, 128/256/512/1024 fused with that tile size.
-int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L) {
+// kernel: 1 two-kernel, 128/256/512/1024 fused with that tile size, 0
+// automatic: FP64 takes the two-kernel stage (it spends fewer FP64 operations);
+// the other precisions take the largest tile that still gives every SM a tile
+// of its own, or the two-kernel stage when even 128-cell tiles would leave SMs
+// idle.  The two-kernel stage shrinks its blocks (down to 32 threads) for the
+// same reason.
+int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L, int sms) {
     L = Layout{};
     L.np = (M.n_cell + PLANE_ALIGN - 1) / PLANE_ALIGN * PLANE_ALIGN;
     L.n_face = M.n_face;
@@ -188,9 +203,18 @@ int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L) {
     const size_t R = real_size(prec), S = state_bytes(prec);
     if (kernel != 0 && kernel != 1 && kernel != 128 && kernel != 256 && kernel != 512 && kernel != 1024)
         return fail(FVLBM_ERR_ARG, "params.kernel = %d: use 0, 1, 128, 256, 512 or 1024", kernel);
-    L.strategy = (kernel == 1 || (kernel == 0 && prec == FVLBM_FP64)) ? STRATEGY_TWO_KERNEL : STRATEGY_TILE;
+    int tile = kernel;
+    if (kernel == 0) {
+        tile = 0;
+        for (int t = 1024; t >= 128 && !tile; t /= 2)
+            if ((M.n_cell + t - 1) / t >= sms) tile = t;
+        if (prec == FVLBM_FP64) tile = 0;
+    }
+    L.strategy = tile == 0 || tile == 1 ? STRATEGY_TWO_KERNEL : STRATEGY_TILE;
+    L.block = 256;
+    while (L.block > 32 && (M.n_cell + L.block - 1) / L.block < 2 * sms) L.block /= 2;
     if (L.strategy == STRATEGY_TILE) {
-        make_tiles(M, L.np, L.maxf, kernel == 0 ? 256 : kernel, L.tp);
+        make_tiles(M, L.np, L.maxf, tile, L.tp);
         const size_t smem = tile_smem_bytes_for(L.tp.lmax, L.tp.gmax, (int)R);
         if (smem > SMEM_LIMIT || L.tp.lmax >= 0xFFFF) {
             if (kernel != 0)
@@ -340,7 +364,7 @@ extern "C" int fvlbm_workspace_bytes(const fvlbm_mesh* mesh, const fvlbm_params*
     if (rc) return rc;
     Layout L;
     try {
-        rc = make_layout(mesh->m, params[0].precision, params[0].scheme, params[0].kernel, L);
+        rc = make_layout(mesh->m, params[0].precision, params[0].scheme, params[0].kernel, L, device_sms(params[0].device));
     } catch (const std::bad_alloc&) {
         return fail(FVLBM_ERR_OOM, "fvlbm_workspace_bytes: out of host memory");
     }
@@ -411,7 +435,7 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
     // layout, workspace
     Layout L;
     try {
-        rc = make_layout(M, s->prec, s->scheme, p0.kernel, L);
+        rc = make_layout(M, s->prec, s->scheme, p0.kernel, L, device_sms(p0.device));
     } catch (const std::bad_alloc&) {
         return fail(FVLBM_ERR_OOM, "fvlbm_init: out of host memory");
     }
@@ -509,6 +533,7 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
     v.n_chunk = (int64_t)chunks.size() / 3;
     v.flag = (int32_t*)(base + L.off_flag);
     v.strategy = L.strategy;
+    v.block = L.block;
     if (L.strategy == STRATEGY_TILE) {
         v.tile = L.tp.tile;
         v.n_tiles = L.tp.n_tiles;

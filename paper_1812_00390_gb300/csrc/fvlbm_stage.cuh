@@ -395,14 +395,15 @@ static int stage_t(const DevView& v, cudaStream_t st, const void* fin, const voi
         }
         return check_launch("fused stage kernel");
     }
-    const unsigned g = grid_of(v.n_cell, 256);
-    if (v.maxf == 4) face_values_kernel<T, S, 4, DEV><<<g, 256, 0, st>>>(v, (const S*)fin);
-    else face_values_kernel<T, S, 8, DEV><<<g, 256, 0, st>>>(v, (const S*)fin);
+    const int bs = v.block > 0 ? v.block : 256;   // smaller blocks spread small meshes over all SMs
+    const unsigned g = grid_of(v.n_cell, bs);
+    if (v.maxf == 4) face_values_kernel<T, S, 4, DEV><<<g, bs, 0, st>>>(v, (const S*)fin);
+    else face_values_kernel<T, S, 8, DEV><<<g, bs, 0, st>>>(v, (const S*)fin);
     if (ev) cudaEventRecord((cudaEvent_t)ev[1], st);
     if (v.maxf == 4)
-        update_kernel<T, S, 4, DEV><<<g, 256, 0, st>>>(v, (const S*)fin, (const S*)fbase, (S*)fout, (T)beta, mode);
+        update_kernel<T, S, 4, DEV><<<g, bs, 0, st>>>(v, (const S*)fin, (const S*)fbase, (S*)fout, (T)beta, mode);
     else
-        update_kernel<T, S, 8, DEV><<<g, 256, 0, st>>>(v, (const S*)fin, (const S*)fbase, (S*)fout, (T)beta, mode);
+        update_kernel<T, S, 8, DEV><<<g, bs, 0, st>>>(v, (const S*)fin, (const S*)fbase, (S*)fout, (T)beta, mode);
     if (ev) cudaEventRecord((cudaEvent_t)ev[2], st);
     return check_launch("stage kernels");
 }

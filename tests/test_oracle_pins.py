@@ -370,6 +370,26 @@ def test_couette_unsteady_series(orc):
     assert np.abs(u[:, 1]).max() < 2e-4
 
 
+def test_couette_steady_linear_profile(orc):
+    """The 32x8 Couette channel run to steady state reaches the linear profile
+    u = y U / H of Sec. 3.1 (measured 2.8e-5 of U = 0.1: O(h^2) on the jittered
+    mesh), with v ~ 0 and rho ~ 1; the steady state is the fixed point RHS = 0,
+    so it does not depend on dt (two dt agree to 1e-12)."""
+    m = mg.couette()
+    o = orc.Oracle(m)
+    _, c, _ = o.geometry()
+    tau = 0.24
+    res = []
+    for dt, n in ((0.06, 30000), (0.04, 45000)):
+        o.set_equilibrium(1.0, (0.0, 0.0))
+        o.run("euler", tau, dt, n)
+        res.append(o.macros())
+    (rho, u), (rho2, u2) = res
+    assert np.abs(u[:, 0] - 0.1 * c[:, 1] / 8.0).max() < 1e-4
+    assert np.abs(u[:, 1]).max() < 5e-5 and np.abs(rho - 1).max() < 5e-5
+    assert np.abs(u2 - u).max() < 1e-12 and np.abs(rho2 - rho).max() < 1e-12
+
+
 def test_couette_spatial_order(orc):
     """Second-order spatial accuracy (Sec. 3.1): L2 error of the unsteady Couette
     profile at fixed time falls at least as h^1.8 from 4 to 16 rows."""
