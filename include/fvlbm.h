@@ -77,8 +77,10 @@ typedef enum fvlbm_scheme {
 typedef enum fvlbm_precision {
     FVLBM_FP64 = 0,     /* f stored and computed in FP64 */
     FVLBM_FP32_DEV = 1, /* g = f - w stored and computed in FP32 */
-    FVLBM_FP16_DEV = 2, /* g stored in FP16 with a power-of-two scale per (instance, a); FP32 math */
-    FVLBM_BF16_DEV = 3  /* g stored in BF16; FP32 math */
+    FVLBM_FP16_DEV = 2, /* split storage: rho - 1 and rho*u in FP32, the non-equilibrium
+                           parts n_a = g_a - g_a^eq (a = 3..8) in FP16, each with a power-of-two scale per
+                           (instance, a); n_0..n_2 follow from the moment constraints; FP32 math */
+    FVLBM_BF16_DEV = 3  /* the same split storage with n_a in BF16; FP32 math */
 } fvlbm_precision;
 
 /* One boundary tag.  Boundary edge i uses bcs[btag[i]]. */

@@ -31,9 +31,9 @@ __device__ __forceinline__ void moments(const T* f, T& r, T& ux, T& uy) {
         my += T(EYA(a)) * f[a];
     }
     r = s;
-    const T rho = DEV ? T(1) + s : s;
-    ux = mx / rho;
-    uy = my / rho;
+    const T inv_rho = T(1) / (DEV ? T(1) + s : s);
+    ux = mx * inv_rho;
+    uy = my * inv_rho;
 }
 
 // Eq. (feq).  FP64 mode: r = rho, returns f^eq.  Deviation mode: r = rho - 1,
@@ -52,13 +52,23 @@ template <typename T, bool DEV>
 __device__ __forceinline__ T rarg(double rho) { return DEV ? T(rho - 1.0) : T(rho); }
 
 // ------------------------------------------------------------------ storage
+// Per-cell arrays are stored in blocks of BLK = 32 consecutive cells (internal
+// order): a block holds component 0 of its 32 cells, then component 1, ...  A
+// cell's component c sits at (i / 32) * ncomp * 32 + c * 32 + i % 32, so a
+// warp of consecutive cells reads whole 128-byte lines, and one address per
+// cell serves every component (constant offsets c * 32).
+__host__ __device__ __forceinline__ int64_t blk_index(int64_t i, int ncomp) {
+    return (i >> BLK_SHIFT) * ((int64_t)ncomp << BLK_SHIFT) + (i & (BLK - 1));
+}
+
 // Whole-cell access to the stored state (T: arithmetic type, DEV: deviation
 // mode, the stored quantity is g = f - w).
-//  double / float   plane a (a = 0..8) holds g_a (f_a in FP64 mode).
-//  __half / bf16    split format: planes 0..2 hold rho - 1, rho u_x, rho u_y in
-//                   FP32; the next six 16-bit planes hold the non-equilibrium
-//                   parts n_a = g_a - g^eq_a(rho, u) of directions a = 3..8,
-//                   times a power-of-two scale per (instance, direction).
+//  double / float   9 components per cell: g_a (f_a in FP64 mode).
+//  __half / bf16    split format: 3 FP32 components rho - 1, rho u_x, rho u_y,
+//                   then six 16-bit components: the non-equilibrium parts
+//                   n_a = g_a - g^eq_a(rho, u) of directions a = 3..8, times
+//                   a power-of-two scale per (instance, direction).  A block
+//                   is 32 x 3 floats followed by 32 x 6 16-bit values.
 //                   n_0, n_1, n_2 follow from sum_a n_a = 0 and
 //                   sum_a e_a n_a = 0 (the non-equilibrium part carries no mass
 //                   or momentum), so rho and u never round through 16 bits;
@@ -67,24 +77,23 @@ template <typename S> struct CellIO;
 
 template <typename S> struct PlainIO {
     template <typename T, bool DEV>
-    __device__ static void load(const void* base, int64_t i, int64_t np, const InstParam&, T* f) {
-        const S* p = (const S*)base;
+    __device__ static void load(const void* base, int64_t i, const InstParam&, T* f) {
+        const S* p = (const S*)base + blk_index(i, FVLBM_Q);
 #pragma unroll
-        for (int a = 0; a < FVLBM_Q; a++) f[a] = (T)p[a * np + i];
+        for (int a = 0; a < FVLBM_Q; a++) f[a] = (T)p[a * BLK];
     }
     template <typename T, bool DEV>
-    __device__ static void store(void* base, int64_t i, int64_t np, const InstParam&, const T* f) {
-        S* p = (S*)base;
+    __device__ static void store(void* base, int64_t i, const InstParam&, const T* f) {
+        S* p = (S*)base + blk_index(i, FVLBM_Q);
 #pragma unroll
-        for (int a = 0; a < FVLBM_Q; a++) p[a * np + i] = (S)f[a];
+        for (int a = 0; a < FVLBM_Q; a++) p[a * BLK] = (S)f[a];
     }
     // FP64 moments of the stored state: r = sum f (FP64 mode) or sum g (deviation), j = sum e g
-    __device__ static void moments64(const void* base, int64_t i, int64_t np, const InstParam&, double& r, double& jx,
-                                     double& jy) {
-        const S* p = (const S*)base;
+    __device__ static void moments64(const void* base, int64_t i, const InstParam&, double& r, double& jx, double& jy) {
+        const S* p = (const S*)base + blk_index(i, FVLBM_Q);
         r = jx = jy = 0;
         for (int a = 0; a < FVLBM_Q; a++) {
-            const double x = (double)p[a * np + i];
+            const double x = (double)p[a * BLK];
             r += x;
             jx += EXA(a) * x;
             jy += EYA(a) * x;
@@ -103,17 +112,25 @@ template <> __device__ __forceinline__ __half f2h<__half>(float x) { return __fl
 template <> __device__ __forceinline__ __nv_bfloat16 f2h<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
 
 template <typename H> struct SplitIO {
+    static constexpr int64_t BLOCK_BYTES = BLK * (3 * sizeof(float) + 6 * sizeof(H));
+    __device__ static const float* cptr(const void* base, int64_t i) {
+        return (const float*)((const unsigned char*)base + (i >> BLK_SHIFT) * BLOCK_BYTES) + (i & (BLK - 1));
+    }
+    __device__ static const H* hptr(const void* base, int64_t i) {
+        return (const H*)((const unsigned char*)base + (i >> BLK_SHIFT) * BLOCK_BYTES + 3 * BLK * sizeof(float)) +
+               (i & (BLK - 1));
+    }
     template <typename T, bool DEV>
-    __device__ static void load(const void* base, int64_t i, int64_t np, const InstParam& P, T* f) {
-        const float* c = (const float*)base;
-        const H* h = (const H*)(c + 3 * np);
-        const float dr = c[i], jx = c[np + i], jy = c[2 * np + i];
+    __device__ static void load(const void* base, int64_t i, const InstParam& P, T* f) {
+        const float* c = cptr(base, i);
+        const H* h = hptr(base, i);
+        const float dr = c[0], jx = c[BLK], jy = c[2 * BLK];
         const float rho = 1.0f + dr, ux = jx / rho, uy = jy / rho;
         float n[FVLBM_Q];
         float s = 0, sx = 0, sy = 0;
 #pragma unroll
         for (int a = 3; a < FVLBM_Q; a++) {
-            n[a] = h2f<H>(h[(a - 3) * np + i]) * P.inv_scale[a];
+            n[a] = h2f<H>(h[(a - 3) * BLK]) * P.inv_scale[a];
             s += n[a];
             sx += float(EXA(a)) * n[a];
             sy += float(EYA(a)) * n[a];
@@ -125,9 +142,9 @@ template <typename H> struct SplitIO {
         for (int a = 0; a < FVLBM_Q; a++) f[a] = (T)(feqs<float, true>(a, dr, ux, uy) + n[a]);
     }
     template <typename T, bool DEV>
-    __device__ static void store(void* base, int64_t i, int64_t np, const InstParam& P, const T* f) {
-        float* c = (float*)base;
-        H* h = (H*)(c + 3 * np);
+    __device__ static void store(void* base, int64_t i, const InstParam& P, const T* f) {
+        float* c = (float*)cptr(base, i);
+        H* h = (H*)hptr(base, i);
         float dr = 0, jx = 0, jy = 0;
 #pragma unroll
         for (int a = 0; a < FVLBM_Q; a++) {
@@ -135,24 +152,43 @@ template <typename H> struct SplitIO {
             jx += float(EXA(a)) * (float)f[a];
             jy += float(EYA(a)) * (float)f[a];
         }
-        c[i] = dr;
-        c[np + i] = jx;
-        c[2 * np + i] = jy;
+        c[0] = dr;
+        c[BLK] = jx;
+        c[2 * BLK] = jy;
         const float rho = 1.0f + dr, ux = jx / rho, uy = jy / rho;
 #pragma unroll
         for (int a = 3; a < FVLBM_Q; a++)
-            h[(a - 3) * np + i] = f2h<H>(((float)f[a] - feqs<float, true>(a, dr, ux, uy)) * P.scale[a]);
+            h[(a - 3) * BLK] = f2h<H>(((float)f[a] - feqs<float, true>(a, dr, ux, uy)) * P.scale[a]);
     }
-    __device__ static void moments64(const void* base, int64_t i, int64_t np, const InstParam&, double& r, double& jx,
-                                     double& jy) {
-        const float* c = (const float*)base;
-        r = c[i];
-        jx = c[np + i];
-        jy = c[2 * np + i];
+    __device__ static void moments64(const void* base, int64_t i, const InstParam&, double& r, double& jx, double& jy) {
+        const float* c = cptr(base, i);
+        r = c[0];
+        jx = c[BLK];
+        jy = c[2 * BLK];
     }
     static constexpr size_t bytes_per_cell = 3 * sizeof(float) + 6 * sizeof(H);
 };
 template <> struct CellIO<__half> : SplitIO<__half> {};
 template <> struct CellIO<__nv_bfloat16> : SplitIO<__nv_bfloat16> {};
+
+// Geometry of one cell (same blocked layout): per face slot k a 64-bit
+// descriptor (meta, link) and three 2-vectors of type T: least-squares
+// coefficients (component 3k), face midpoint minus centroid (3k + 1) and
+// face vector over area (3k + 2).
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { typedef float2 type; };
+template <> struct Vec2<double> { typedef double2 type; };
+
+template <typename T, int MAXF> struct GeoRef {
+    typedef typename Vec2<T>::type T2;
+    const uint2* d;
+    const T2* g;
+    __device__ __forceinline__ GeoRef(const void* desc, const void* geo, int64_t i)
+        : d((const uint2*)desc + blk_index(i, MAXF)), g((const T2*)geo + blk_index(i, 3 * MAXF)) {}
+    __device__ __forceinline__ uint2 desc(int k) const { return d[k * BLK]; }
+    __device__ __forceinline__ T2 cg(int k) const { return g[(3 * k) * BLK]; }
+    __device__ __forceinline__ T2 rv(int k) const { return g[(3 * k + 1) * BLK]; }
+    __device__ __forceinline__ T2 nv(int k) const { return g[(3 * k + 2) * BLK]; }
+};
 
 }  // namespace fvlbm

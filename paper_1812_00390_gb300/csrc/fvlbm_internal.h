@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <vector_types.h>
+
 #include "fvlbm.h"
 
 namespace fvlbm {
@@ -78,28 +80,43 @@ struct BcParam {
     double uwx, uwy, rho_inf, uix, uiy;
 };
 
+// Per-cell arrays on the device are blocked: 32 consecutive cells per block,
+// each component of the block contiguous (see blk_index in fvlbm_device.cuh).
+constexpr int BLK_SHIFT = 5;
+constexpr int BLK = 1 << BLK_SHIFT;
+
+// Fused stage: shared-memory capacity of a tile of TILE cells (compile-time
+// strides, so that every shared-memory access is a fixed offset from one
+// index): LS local cells (tile, 1-ring, 2-ring) and FS local faces (the faces
+// of the tile's cells).  The tile planner ends a tile early when its halo or
+// faces would not fit.
+template <int TILE, int MAXF> struct TileDims {
+    static constexpr int LS = 2 * TILE + 128;
+    static constexpr int FS = MAXF <= 4 ? (5 * TILE) / 2 : 4 * TILE;
+};
+// "no local face / neighbour" in a 16-bit link field
+constexpr uint32_t LINK_NONE = 0xFFFF;
+
 // Device pointers of one solver (all inside one workspace).
 struct DevView {
     int64_t n_cell;     // cells (internal numbering 0..n_cell-1)
-    int64_t np;         // padded plane length
-    int64_t n_face;     // face-value table length
+    int64_t np;         // padded cell count (multiple of the largest tile)
+    int64_t n_face;     // face-value table length (two-kernel stage)
     int32_t maxf;       // slots per cell in the packed arrays (4 or 8)
     int32_t n_inst;
-    // geometry, [maxf][np] planes
-    const uint32_t* meta;  // kind | outmask << 8 | bc << 16
-    const void* cg;        // T [2][maxf][np]   least-squares coefficients
-    const void* rv;        // T [2][maxf][np]   face midpoint - centroid
-    const void* nv;        // T [2][maxf][np]   (dy, -dx) / A
-    // two-kernel stage only
+    // geometry, blocked per cell, [maxf] (desc) and [3 maxf] (geo) components
+    const uint2* desc;  // x: kind | outmask << 8 | bc << 16;  y: link (see below)
+    const void* geo;    // T2 [3 maxf]: least-squares coefficients, face midpoint - centroid,
+                        //              face vector / area of each slot
+    // two-kernel stage: desc.y = face id; nbr = neighbour cell, blocked [maxf]
     const int32_t* nbr;
-    const int32_t* fid;
     const double* area;    // [np]
     const int32_t* grp;    // [np] instance of each cell
     const InstParam* inst; // [n_inst]
     const BcParam* bc;     // [n_bc]
     // state
-    void* fa;   // S [9][np]  state
-    void* fb;   // S [9][np]  stage state (multistage schemes)
+    void* fa;   // S blocked [9] (or the split format): the state
+    void* fb;   // same: stage state (multistage schemes) or the other buffer of a ping-pong pair
     void* rprev;// T [9][np]  AB2 previous RHS
     void* fv;   // T [8][n_face] face values of directions 1..8
     double* rho;    // [np]
@@ -112,20 +129,17 @@ struct DevView {
     const int64_t* chunk;   // [n_chunk][3] (begin, end, instance)
     int64_t n_chunk;
     int32_t* flag;  // non-finite flag
-    // fused stage (one CTA per tile of `tile` consecutive cells)
+    // fused stage (one CTA per tile of at most `tile` consecutive cells);
+    // desc.y = tile-local neighbour | tile-local face << 16
     int32_t strategy;        // STRATEGY_TWO_KERNEL or STRATEGY_TILE
     int32_t block;           // threads per block of the two-kernel stage
-    int32_t tile;            // cells per tile (threads per CTA)
+    int32_t tile;            // most cells per tile (threads per CTA)
     int64_t n_tiles;
-    int32_t lmax;            // most local cells (tile + halo) of any tile
-    int32_t gmax;            // most cells with a gradient (tile + 1-ring) of any tile
-    int32_t r1max;           // largest 1-ring of any tile
-    const int64_t* halo_ptr; // [n_tiles + 1] into halo
-    const int32_t* halo;     // 1-ring then 2-ring cells of each tile (global ids)
-    const int32_t* n_r1;     // [n_tiles] 1-ring size
-    const uint16_t* lnbr;    // [maxf][np] tile-local index of the neighbour across each face
-    const uint16_t* r1nbr;   // [halo entries][maxf] tile-local stencil of 1-ring cells
-    const void* rn;          // T [2][maxf][np] neighbour-side face midpoint - neighbour centroid
+    const int64_t* tile_begin; // [n_tiles + 1] first cell of each tile
+    const int64_t* halo_ptr;   // [n_tiles + 1] into halo
+    const int32_t* halo;       // 1-ring then 2-ring cells of each tile (global ids)
+    const int64_t* r1_ptr;     // [n_tiles + 1] 1-ring entries of each tile (running count)
+    const uint32_t* r1link;    // blocked [maxf] over 1-ring entries: local neighbour | local face << 16
 };
 
 enum Strategy { STRATEGY_TWO_KERNEL = 0, STRATEGY_TILE = 1 };
@@ -139,17 +153,10 @@ int launch_stage(const DevView& v, int prec, void* stream, const void* fin, cons
 // Most kernels launched by one stage (two-kernel strategy).
 constexpr int STAGE_KERNELS = 2;
 inline int stage_kernels(const DevView& v) { return v.strategy == STRATEGY_TILE ? 1 : 2; }
-// Dynamic shared memory of the fused stage kernel: f of tile and halo,
-// gradients and macros of tile and 1-ring, the tile's geometry (meta, local
-// neighbour, 4 vectors per slot, instance) and the 1-ring's (meta, local
-// stencil, least-squares vector per slot), for real type of `rsize` bytes.
-// Dynamic shared memory of the fused stage kernel: f of tile and halo, and
-// the gradients of tile and 1-ring cells, for real type of `rsize` bytes.
-inline size_t tile_smem_bytes_for(int lmax, int gmax, int rsize) {
-    return (size_t)rsize * ((size_t)FVLBM_Q * lmax + 2 * (FVLBM_Q - 1) * (size_t)gmax);
-}
-inline size_t tile_smem_bytes(const DevView& v, size_t rsize) {
-    return tile_smem_bytes_for(v.lmax, v.gmax, (int)rsize);
+// Dynamic shared memory of the fused stage kernel: f of the local cells and
+// the face values of the local faces, for real type of `rsize` bytes.
+inline size_t tile_smem_bytes_for(int ls, int fs, int rsize) {
+    return (size_t)rsize * ((size_t)FVLBM_Q * ls + (size_t)(FVLBM_Q - 1) * fs);
 }
 // One translation unit per state precision.
 int stage_fp64(const DevView& v, void* stream, const void* fin, const void* fbase, void* fout, double beta, int mode,

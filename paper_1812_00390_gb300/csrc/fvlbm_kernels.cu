@@ -38,7 +38,7 @@ __global__ void init_eq_kernel(DevView v) {
     const InstParam& P = v.inst[v.grp[i]];
     T f[FVLBM_Q];
     for (int a = 0; a < FVLBM_Q; a++) f[a] = feqs<T, DEV>(a, rarg<T, DEV>(P.rho0), T(P.u0x), T(P.u0y));
-    CellIO<S>::template store<T, DEV>(v.fa, i, v.np, P, f);
+    CellIO<S>::template store<T, DEV>(v.fa, i, P, f);
 }
 
 // rho, u in FP64 from the stored state (Step 6).
@@ -47,7 +47,7 @@ __global__ void macros_kernel(DevView v) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.n_cell) return;
     double r, mx, my;
-    CellIO<S>::moments64(v.fa, i, v.np, v.inst[v.grp[i]], r, mx, my);
+    CellIO<S>::moments64(v.fa, i, v.inst[v.grp[i]], r, mx, my);
     double rho = DEV ? 1.0 + r : r;
     v.rho[i] = rho;
     v.ux[i] = mx / rho;
@@ -60,7 +60,7 @@ __global__ void get_f_kernel(DevView v) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.n_cell) return;
     T f[FVLBM_Q];
-    CellIO<S>::template load<T, DEV>(v.fa, i, v.np, v.inst[v.grp[i]], f);
+    CellIO<S>::template load<T, DEV>(v.fa, i, v.inst[v.grp[i]], f);
     for (int a = 0; a < FVLBM_Q; a++) v.conv[a * v.np + i] = DEV ? (double)f[a] + wgt<double>(a) : (double)f[a];
 }
 
@@ -73,7 +73,7 @@ __global__ void set_f_kernel(DevView v) {
         const double x = v.conv[a * v.np + i];
         f[a] = (T)(DEV ? x - wgt<double>(a) : x);
     }
-    CellIO<S>::template store<T, DEV>(v.fa, i, v.np, v.inst[v.grp[i]], f);
+    CellIO<S>::template store<T, DEV>(v.fa, i, v.inst[v.grp[i]], f);
 }
 
 // Deterministic FP64 reductions: one block per chunk of one instance, fixed

@@ -56,7 +56,7 @@ __global__ void mass_chunks_static_kernel(DevView v, double* part) {
     double s0 = 0;
     for (int64_t i = b + threadIdx.x; i < e; i += NA_THREADS) {
         double r, jx, jy;
-        CellIO<S>::moments64(v.fa, i, v.np, v.inst[v.grp[i]], r, jx, jy);
+        CellIO<S>::moments64(v.fa, i, v.inst[v.grp[i]], r, jx, jy);
         const double rho = DEV ? 1.0 + r : r;
         s0 += v.area[i] * rho;
     }

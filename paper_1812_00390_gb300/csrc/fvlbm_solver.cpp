@@ -37,8 +37,15 @@ struct fvlbm_solver {
     std::vector<InstParam> inst;
     bool ab2_started = false;
     std::vector<double> h_conv, h_rho, h_ux, h_uy;
-    // CUDA graphs of one step and of GRAPH_CHUNK steps, built lazily
-    cudaGraphExec_t g1 = nullptr, gk = nullptr;
+    // single-stage schemes on the fused stage alternate the state between
+    // buf[0] and buf[1] (a tile must not overwrite cells other tiles still
+    // read); v.fa is always the current state, buf[cur]
+    bool pingpong = false;
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    // CUDA graphs of one step and of GRAPH_CHUNK steps, built lazily, one pair
+    // per state buffer the step starts from
+    cudaGraphExec_t g1[2] = {nullptr, nullptr}, gk[2] = {nullptr, nullptr};
     bool graphs_ok = true;
     int64_t direct_steps = 0;
 };
@@ -79,19 +86,25 @@ size_t state_bytes(int prec) {
     return prec == FVLBM_FP64 ? 72 : (prec == FVLBM_FP32_DEV ? 36 : 24);
 }
 
-// Halo structure of the fused stage kernel: tiles of `tile` consecutive cells
-// (internal order); per tile its 1-ring (face neighbours outside the tile) and
-// 2-ring (face neighbours of the 1-ring outside tile and 1-ring), and tile-local
-// indices of every neighbour the kernel reads.
+// Tile structure of the fused stage kernel.  Tiles are runs of consecutive
+// cells (internal order), at most `tile` long and cut shorter where the local
+// cells (tile, 1-ring = face neighbours outside the tile, 2-ring = their face
+// neighbours outside tile and 1-ring) or the tile's faces would exceed the
+// kernel's shared-memory capacity.  Every tile cell slot carries the local
+// index of its neighbour and the local index of its face; every 1-ring slot
+// the local index of its neighbour and, for faces shared with the tile, the
+// local face.
 struct TilePlan {
     int tile = 0;
     int64_t n_tiles = 0;
-    int32_t lmax = 0, gmax = 0, r1max = 0;
-    std::vector<int64_t> halo_ptr;
-    std::vector<int32_t> halo;
-    std::vector<int32_t> n_r1;
-    std::vector<uint16_t> lnbr;   // [maxf][np]
-    std::vector<uint16_t> r1nbr;  // [halo][maxf]
+    std::vector<int64_t> begin;     // [n_tiles + 1]
+    std::vector<int64_t> halo_ptr;  // [n_tiles + 1]
+    std::vector<int32_t> halo;      // 1-ring then 2-ring of each tile
+    std::vector<int64_t> r1_ptr;    // [n_tiles + 1]
+    std::vector<uint32_t> link;     // [n_cell][maxf] local neighbour | local face << 16
+    std::vector<uint32_t> r1link;   // [1-ring entries][maxf] same fields
+    int32_t max_local = 0, max_faces = 0;
+    int64_t short_tiles = 0;        // tiles cut below `tile` cells by the capacity
 };
 
 int64_t internal_nbr(const Mesh& M, int64_t i, int k) {
@@ -99,67 +112,144 @@ int64_t internal_nbr(const Mesh& M, int64_t i, int k) {
     return S.kind == SK_INTERIOR ? M.iperm[S.nb] : -1;
 }
 
-void make_tiles(const Mesh& M, int64_t np, int maxf, int tile, TilePlan& P) {
-    const int64_t n = M.n_cell;
-    P.tile = tile;
-    P.n_tiles = (n + tile - 1) / tile;
-    P.halo_ptr.assign(P.n_tiles + 1, 0);
-    P.n_r1.assign(P.n_tiles, 0);
-    P.lnbr.assign((size_t)maxf * np, 0xFFFF);
-    P.halo.clear();
-    std::vector<int64_t> stamp(n, -1);
-    std::vector<int32_t> loc(n, 0);
-    std::vector<int64_t> r1;
-    std::vector<uint16_t> r1nbr;
-    P.lmax = P.gmax = 0;
-    for (int64_t t = 0; t < P.n_tiles; t++) {
-        const int64_t c0 = t * tile, c1 = std::min(n, c0 + tile);
-        int32_t nl = 0;
-        for (int64_t i = c0; i < c1; i++) {
-            stamp[i] = t;
-            loc[i] = nl++;
-        }
-        r1.clear();
-        for (int64_t i = c0; i < c1; i++)
-            for (int k = 0; k < M.nf[M.perm[i]]; k++) {
-                const int64_t j = internal_nbr(M, i, k);
-                if (j >= 0 && stamp[j] != t) {
-                    stamp[j] = t;
-                    loc[j] = nl++;
-                    r1.push_back(j);
-                    P.halo.push_back((int32_t)j);
-                }
-            }
-        const int32_t n1 = (int32_t)r1.size();
-        for (int64_t j : r1)
-            for (int k = 0; k < M.nf[M.perm[j]]; k++) {
-                const int64_t q = internal_nbr(M, j, k);
-                if (q >= 0 && stamp[q] != t) {
-                    stamp[q] = t;
-                    loc[q] = nl++;
-                    P.halo.push_back((int32_t)q);
-                }
-            }
-        for (int64_t i = c0; i < c1; i++)
-            for (int k = 0; k < M.nf[M.perm[i]]; k++) {
-                const int64_t j = internal_nbr(M, i, k);
-                if (j >= 0) P.lnbr[(size_t)k * np + i] = (uint16_t)loc[j];
-            }
-        // stencil of every halo entry (only the 1-ring's are read)
-        const size_t base = r1nbr.size();
-        r1nbr.resize(base + (size_t)(P.halo.size() - P.halo_ptr[t]) * maxf, 0xFFFF);
-        for (int32_t q = 0; q < n1; q++)
-            for (int k = 0; k < M.nf[M.perm[r1[q]]]; k++) {
-                const int64_t j = internal_nbr(M, r1[q], k);
-                if (j >= 0) r1nbr[base + (size_t)q * maxf + k] = (uint16_t)loc[j];
-            }
-        P.halo_ptr[t + 1] = (int64_t)P.halo.size();
-        P.n_r1[t] = n1;
-        P.lmax = std::max(P.lmax, nl);
-        P.gmax = std::max<int32_t>(P.gmax, (int32_t)(c1 - c0) + n1);
-        P.r1max = std::max<int32_t>(P.r1max, n1);
+// Shared-memory capacity of the fused kernel for a tile size (TileDims).
+bool tile_dims(int tile, int maxf, int& ls, int& fs) {
+#define FVLBM_TD(T_)                                                                    \
+    case T_:                                                                            \
+        ls = maxf <= 4 ? TileDims<T_, 4>::LS : TileDims<T_, 8>::LS;                     \
+        fs = maxf <= 4 ? TileDims<T_, 4>::FS : TileDims<T_, 8>::FS;                     \
+        return true;
+    switch (tile) {
+        FVLBM_TD(128)
+        FVLBM_TD(256)
+        FVLBM_TD(512)
+        FVLBM_TD(1024)
     }
-    P.r1nbr.swap(r1nbr);
+#undef FVLBM_TD
+    return false;
+}
+
+struct TileScratch {
+    std::vector<int64_t> stamp;
+    std::vector<int32_t> loc;
+    std::vector<int64_t> r1, r2;
+    std::vector<int32_t> t_nb, t_f, r_nb, r_f;
+    int64_t gen = 0;
+};
+
+// Local numbering of the tile [c0, c0 + len): tile cells, 1-ring, 2-ring, and
+// the local faces of the tile cells.  False when it exceeds ls / fs.
+bool try_tile(const Mesh& M, int maxf, int64_t c0, int len, int ls, int fs, TileScratch& W, int& n_local,
+              int& n_faces) {
+    const int64_t g = ++W.gen;
+    int nl = 0;
+    for (int64_t i = c0; i < c0 + len; i++) {
+        W.stamp[i] = g;
+        W.loc[i] = nl++;
+    }
+    W.r1.clear();
+    W.r2.clear();
+    for (int64_t i = c0; i < c0 + len; i++)
+        for (int k = 0; k < M.nf[M.perm[i]]; k++) {
+            const int64_t j = internal_nbr(M, i, k);
+            if (j >= 0 && W.stamp[j] != g) {
+                W.stamp[j] = g;
+                W.loc[j] = nl++;
+                W.r1.push_back(j);
+            }
+        }
+    for (int64_t j : W.r1)
+        for (int k = 0; k < M.nf[M.perm[j]]; k++) {
+            const int64_t q = internal_nbr(M, j, k);
+            if (q >= 0 && W.stamp[q] != g) {
+                W.stamp[q] = g;
+                W.loc[q] = nl++;
+                W.r2.push_back(q);
+            }
+        }
+    if (nl > ls) return false;
+    const int n1 = (int)W.r1.size();
+    W.t_nb.assign((size_t)len * maxf, -1);
+    W.t_f.assign((size_t)len * maxf, -1);
+    W.r_nb.assign((size_t)n1 * maxf, -1);
+    W.r_f.assign((size_t)n1 * maxf, -1);
+    int nf = 0;
+    for (int li = 0; li < len; li++) {
+        const int64_t i = c0 + li;
+        const int64_t c = M.perm[i];
+        for (int k = 0; k < M.nf[c]; k++) {
+            const Slot& S = M.slots[(size_t)c * MAXP + k];
+            const size_t x = (size_t)li * maxf + k;
+            if (S.kind == SK_INTERIOR) {
+                const int lj = W.loc[M.iperm[S.nb]];
+                W.t_nb[x] = lj;
+                if (W.t_f[x] < 0) {
+                    W.t_f[x] = nf;
+                    if (lj < len) W.t_f[(size_t)lj * maxf + S.nb_slot] = nf;
+                    else W.r_f[(size_t)(lj - len) * maxf + S.nb_slot] = nf;
+                    nf++;
+                }
+            } else {
+                W.t_f[x] = nf++;
+            }
+        }
+    }
+    if (nf > fs) return false;
+    for (int e = 0; e < n1; e++)
+        for (int k = 0; k < M.nf[M.perm[W.r1[e]]]; k++) {
+            const int64_t q = internal_nbr(M, W.r1[e], k);
+            if (q >= 0) W.r_nb[(size_t)e * maxf + k] = W.loc[q];
+        }
+    n_local = nl;
+    n_faces = nf;
+    return true;
+}
+
+uint32_t pack_link(int nb, int f) {
+    return (uint32_t)(nb < 0 ? LINK_NONE : (uint32_t)nb) | ((uint32_t)(f < 0 ? LINK_NONE : (uint32_t)f) << 16);
+}
+
+int make_tiles(const Mesh& M, int maxf, int tile, TilePlan& P) {
+    int ls = 0, fs = 0;
+    if (!tile_dims(tile, maxf, ls, fs)) return fail(FVLBM_ERR_ARG, "unsupported tile size %d", tile);
+    const int64_t n = M.n_cell;
+    P = TilePlan{};
+    P.tile = tile;
+    P.begin.push_back(0);
+    P.halo_ptr.push_back(0);
+    P.r1_ptr.push_back(0);
+    P.link.assign((size_t)n * maxf, 0xFFFFFFFFu);
+    TileScratch W;
+    W.stamp.assign(n, 0);
+    W.loc.assign(n, 0);
+    int64_t c0 = 0;
+    while (c0 < n) {
+        int len = (int)std::min<int64_t>(tile, n - c0);
+        int nl = 0, nf = 0;
+        while (!try_tile(M, maxf, c0, len, ls, fs, W, nl, nf)) {
+            if (len == 1)
+                return fail(FVLBM_ERR_UNSUPPORTED, "cell %lld: its halo exceeds the fused stage's capacity",
+                            (long long)c0);
+            len = len > BLK ? (len - 1) / BLK * BLK : len / 2;
+        }
+        if (len < std::min<int64_t>(tile, n - c0)) P.short_tiles++;
+        for (int li = 0; li < len; li++)
+            for (int k = 0; k < maxf; k++) {
+                const size_t x = (size_t)li * maxf + k;
+                if (W.t_f[x] >= 0) P.link[(size_t)(c0 + li) * maxf + k] = pack_link(W.t_nb[x], W.t_f[x]);
+            }
+        for (int64_t j : W.r1) P.halo.push_back((int32_t)j);
+        for (int64_t q : W.r2) P.halo.push_back((int32_t)q);
+        for (size_t x = 0; x < W.r_nb.size(); x++) P.r1link.push_back(pack_link(W.r_nb[x], W.r_f[x]));
+        c0 += len;
+        P.begin.push_back(c0);
+        P.halo_ptr.push_back((int64_t)P.halo.size());
+        P.r1_ptr.push_back(P.r1_ptr.back() + (int64_t)W.r1.size());
+        P.max_local = std::max(P.max_local, nl);
+        P.max_faces = std::max(P.max_faces, nf);
+    }
+    P.n_tiles = (int64_t)P.begin.size() - 1;
+    return FVLBM_OK;
 }
 
 // Offsets of every array inside the workspace (0 size when a strategy does not use it).
@@ -168,10 +258,11 @@ struct Layout {
     int maxf;
     int strategy;
     int block;
+    bool pingpong;   // single-stage scheme on the fused stage: the state alternates between fa and fb
     TilePlan tp;
-    size_t off_nbr, off_fid, off_meta, off_cg, off_rv, off_nv, off_area, off_grp, off_inst, off_bc,
-        off_fa, off_fb, off_rprev, off_fv, off_rho, off_ux, off_uy, off_uold, off_part, off_red, off_conv,
-        off_chunk, off_flag, off_hptr, off_halo, off_nr1, off_lnbr, off_r1nbr, off_rn, total;
+    size_t off_desc, off_geo, off_nbr, off_area, off_grp, off_inst, off_bc, off_fa, off_fb, off_rprev, off_fv,
+        off_rho, off_ux, off_uy, off_uold, off_part, off_red, off_conv, off_chunk, off_flag, off_tbegin, off_hptr,
+        off_halo, off_r1ptr, off_r1link, total;
 };
 
 constexpr size_t SMEM_LIMIT = 227 * 1024;
@@ -185,7 +276,9 @@ int device_sms(int device) {
     }
     return n;
 }
-constexpr int64_t PLANE_ALIGN = 1024;  // planes hold whole tiles of the largest tile size
+constexpr int64_t PLANE_ALIGN = 1024;  // cell arrays hold whole blocks and whole tiles of the largest size
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 // kernel: 1 two-kernel, 128/256/512/1024 fused with that tile size, 0
 // automatic: FP64 takes the two-kernel stage (it spends fewer FP64 operations);
@@ -195,7 +288,7 @@ constexpr int64_t PLANE_ALIGN = 1024;  // planes hold whole tiles of the largest
 // same reason.
 int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L, int sms) {
     L = Layout{};
-    L.np = (M.n_cell + PLANE_ALIGN - 1) / PLANE_ALIGN * PLANE_ALIGN;
+    L.np = round_up(M.n_cell, PLANE_ALIGN);
     L.n_face = M.n_face;
     L.maxf = M.max_faces <= 4 ? 4 : 8;
     L.n_chunk = 0;
@@ -214,17 +307,17 @@ int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L, int 
     L.block = 256;
     while (L.block > 32 && (M.n_cell + L.block - 1) / L.block < 2 * sms) L.block /= 2;
     if (L.strategy == STRATEGY_TILE) {
-        make_tiles(M, L.np, L.maxf, tile, L.tp);
-        const size_t smem = tile_smem_bytes_for(L.tp.lmax, L.tp.gmax, (int)R);
-        if (smem > SMEM_LIMIT || L.tp.lmax >= 0xFFFF) {
-            if (kernel != 0)
-                return fail(FVLBM_ERR_UNSUPPORTED, "fused stage needs %zu B of shared memory per tile (limit %zu)",
-                            smem, SMEM_LIMIT);
-            L.strategy = STRATEGY_TWO_KERNEL;
-            L.tp = TilePlan{};
-        }
+        int ls = 0, fs = 0;
+        tile_dims(tile, L.maxf, ls, fs);
+        const size_t smem = tile_smem_bytes_for(ls, fs, (int)R);
+        if (smem > SMEM_LIMIT)
+            return fail(FVLBM_ERR_UNSUPPORTED, "fused stage with %d-cell tiles needs %zu B of shared memory (limit %zu)",
+                        tile, smem, SMEM_LIMIT);
+        int rc = make_tiles(M, L.maxf, tile, L.tp);
+        if (rc) return rc;
     }
     const bool tiled = L.strategy == STRATEGY_TILE, two = !tiled;
+    L.pingpong = tiled && (scheme == FVLBM_EULER || scheme == FVLBM_AB2);
     size_t o = 0;
     auto take = [&](size_t bytes) {
         size_t r = o;
@@ -232,24 +325,21 @@ int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L, int 
         return r;
     };
     const size_t plane = (size_t)L.np, slots = plane * L.maxf;
-    L.off_meta = take(4 * slots);
+    const size_t n_r1 = tiled ? (size_t)round_up(L.tp.r1_ptr.back(), BLK) : 0;
+    L.off_desc = take(8 * slots);
+    L.off_geo = take(2 * R * 3 * slots);
+    L.off_nbr = take(two ? 4 * slots : 0);
     L.off_area = take(8 * plane);
     L.off_grp = take(4 * plane);
     L.off_inst = take(sizeof(InstParam) * M.n_inst);
     L.off_bc = take(sizeof(BcParam) * std::max<size_t>(1, M.bcs.size()));
-    L.off_nbr = take(two ? 4 * slots : 0);
-    L.off_fid = take(two ? 4 * slots : 0);
-    L.off_cg = take(R * slots * 2);
-    L.off_rv = take(R * slots * 2);
-    L.off_nv = take(R * slots * 2);
+    L.off_tbegin = take(tiled ? 8 * (size_t)(L.tp.n_tiles + 1) : 0);
     L.off_hptr = take(tiled ? 8 * (size_t)(L.tp.n_tiles + 1) : 0);
     L.off_halo = take(tiled ? 4 * L.tp.halo.size() : 0);
-    L.off_nr1 = take(tiled ? 4 * (size_t)L.tp.n_tiles : 0);
-    L.off_lnbr = take(tiled ? 2 * slots : 0);
-    L.off_r1nbr = take(tiled ? 2 * L.tp.r1nbr.size() : 0);
-    L.off_rn = take(tiled ? R * slots * 2 : 0);
+    L.off_r1ptr = take(tiled ? 8 * (size_t)(L.tp.n_tiles + 1) : 0);
+    L.off_r1link = take(tiled ? 4 * n_r1 * L.maxf : 0);
     L.off_fa = take(S * plane);   // everything before this is uploaded once
-    L.off_fb = (scheme == FVLBM_RK2 || scheme == FVLBM_RK4) ? take(S * plane) : 0;
+    L.off_fb = (scheme == FVLBM_RK2 || scheme == FVLBM_RK4 || L.pingpong) ? take(S * plane) : 0;
     L.off_rprev = scheme == FVLBM_AB2 ? take(R * plane * FVLBM_Q) : 0;
     L.off_fv = take(two ? R * (size_t)std::max<int64_t>(1, L.n_face) * (FVLBM_Q - 1) : 0);
     L.off_rho = take(8 * plane);
@@ -295,25 +385,45 @@ double instance_umax(const Mesh& M, int k, const fvlbm_params& p) {
     return u;
 }
 
+// Index of component c of cell i in a blocked array of ncomp components.
+inline size_t blk(int64_t i, int c, int ncomp) {
+    return (size_t)((i >> BLK_SHIFT) * ((int64_t)ncomp << BLK_SHIFT) + ((int64_t)c << BLK_SHIFT) + (i & (BLK - 1)));
+}
+
+// Writer mask of an interior slot: the directions whose face value this side
+// computes -- those it is upwind for (e.n > 0) and, for directions parallel
+// to the face (e.n = 0, zero flux), the side with the smaller (cell, slot) so
+// that every (face, direction) has exactly one finite writer.
+uint32_t writer_mask(const Slot& S, int64_t i, int k, int64_t j) {
+    static const int EXI[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    static const int EYI[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    uint32_t m = S.outmask;
+    const bool first = i < j || (i == j && k < S.nb_slot);
+    if (first)
+        for (int a = 1; a < FVLBM_Q; a++)
+            if (EXI[a] * S.nx + EYI[a] * S.ny == 0.0) m |= 1u << (a - 1);
+    return m;
+}
+
 template <typename T>
 void pack_geometry(const Mesh& M, const Layout& L, std::vector<unsigned char>& host) {
-    const int64_t n = M.n_cell, np = L.np;
+    const int64_t n = M.n_cell;
     const int maxf = L.maxf;
     const bool two = L.strategy == STRATEGY_TWO_KERNEL;
     unsigned char* H = host.data();
-    uint32_t* meta = (uint32_t*)(H + L.off_meta);
+    uint32_t* desc = (uint32_t*)(H + L.off_desc);   // pairs (x, y)
+    T* geo = (T*)(H + L.off_geo);                   // pairs of T
     double* area = (double*)(H + L.off_area);
     int32_t* grp = (int32_t*)(H + L.off_grp);
     int32_t* nbr = two ? (int32_t*)(H + L.off_nbr) : nullptr;
-    int32_t* fid = two ? (int32_t*)(H + L.off_fid) : nullptr;
-    T* cg = (T*)(H + L.off_cg);
-    T* rv = (T*)(H + L.off_rv);
-    T* nv = (T*)(H + L.off_nv);
-    T* rn = two ? nullptr : (T*)(H + L.off_rn);
-    for (int64_t x = 0; x < (int64_t)maxf * np; x++) {
-        meta[x] = SK_NONE;
-        if (two) nbr[x] = fid[x] = -1;
+    for (size_t x = 0; x < (size_t)maxf * L.np; x++) {
+        desc[2 * x] = SK_NONE;
+        desc[2 * x + 1] = 0xFFFFFFFFu;
+        if (two) nbr[x] = -1;
     }
+    // face ids of the two-kernel face table: both slots of an interior face share one
+    std::vector<int32_t> fid;
+    if (two) fid.assign((size_t)n * maxf, -1);
     int64_t next = 0;
     int32_t g = 0;
     for (int64_t i = 0; i < n; i++) {
@@ -323,34 +433,36 @@ void pack_geometry(const Mesh& M, const Layout& L, std::vector<unsigned char>& h
         area[i] = M.area[c];
         for (int k = 0; k < M.nf[c]; k++) {
             const Slot& S = M.slots[(size_t)c * MAXP + k];
-            const int64_t x = (int64_t)k * np + i;
-            meta[x] = (uint32_t)S.kind | (S.outmask << 8) | ((uint32_t)(S.bc < 0 ? 0 : S.bc) << 16);
+            const size_t d = blk(i, k, maxf);
+            const int64_t j = S.kind == SK_INTERIOR ? M.iperm[S.nb] : -1;
+            const uint32_t mask = S.kind == SK_INTERIOR ? writer_mask(S, i, k, j) : S.outmask;
+            desc[2 * d] = (uint32_t)S.kind | (mask << 8) | ((uint32_t)(S.bc < 0 ? 0 : S.bc) << 16);
             if (two) {
-                if (S.kind == SK_INTERIOR) {
-                    const int64_t j = M.iperm[S.nb];
-                    nbr[x] = (int32_t)j;
-                    if (fid[x] < 0) {
-                        fid[x] = (int32_t)next;
-                        fid[(int64_t)S.nb_slot * np + j] = (int32_t)next;
-                        next++;
-                    }
-                } else {
-                    fid[x] = (int32_t)next++;
+                int32_t& f = fid[(size_t)i * maxf + k];
+                if (f < 0) {
+                    f = (int32_t)next++;
+                    if (j >= 0) fid[(size_t)j * maxf + S.nb_slot] = f;
                 }
+                desc[2 * d + 1] = (uint32_t)f;
+                nbr[d] = (int32_t)j;
+            } else {
+                desc[2 * d + 1] = L.tp.link[(size_t)i * maxf + k];
             }
-            cg[(0 * maxf + k) * np + i] = (T)S.cgx;
-            cg[(1 * maxf + k) * np + i] = (T)S.cgy;
-            rv[(0 * maxf + k) * np + i] = (T)(S.px - M.cx[c]);
-            rv[(1 * maxf + k) * np + i] = (T)(S.py - M.cy[c]);
-            nv[(0 * maxf + k) * np + i] = (T)(S.nx / M.area[c]);
-            nv[(1 * maxf + k) * np + i] = (T)(S.ny / M.area[c]);
-            if (rn && S.kind == SK_INTERIOR) {
-                // the neighbour's own reconstruction vector to this face
-                const Slot& Q = M.slots[(size_t)S.nb * MAXP + S.nb_slot];
-                rn[(0 * maxf + k) * np + i] = (T)(Q.px - M.cx[S.nb]);
-                rn[(1 * maxf + k) * np + i] = (T)(Q.py - M.cy[S.nb]);
-            }
+            const size_t q0 = blk(i, 3 * k, 3 * maxf), q1 = blk(i, 3 * k + 1, 3 * maxf), q2 = blk(i, 3 * k + 2, 3 * maxf);
+            geo[2 * q0] = (T)S.cgx;
+            geo[2 * q0 + 1] = (T)S.cgy;
+            geo[2 * q1] = (T)(S.px - M.cx[c]);
+            geo[2 * q1 + 1] = (T)(S.py - M.cy[c]);
+            geo[2 * q2] = (T)(S.nx / M.area[c]);
+            geo[2 * q2 + 1] = (T)(S.ny / M.area[c]);
         }
+    }
+    if (!two) {
+        uint32_t* r1 = (uint32_t*)(H + L.off_r1link);
+        const int64_t ne = L.tp.r1_ptr.back();
+        for (int64_t e = 0; e < (int64_t)round_up(ne, BLK); e++)
+            for (int k = 0; k < maxf; k++)
+                r1[blk(e, k, maxf)] = e < ne ? L.tp.r1link[(size_t)e * maxf + k] : 0xFFFFFFFFu;
     }
 }
 
@@ -463,11 +575,10 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
         if (s->prec == FVLBM_FP64) pack_geometry<double>(M, L, host);
         else pack_geometry<float>(M, L, host);
         if (L.strategy == STRATEGY_TILE) {
+            std::memcpy(host.data() + L.off_tbegin, L.tp.begin.data(), 8 * L.tp.begin.size());
             std::memcpy(host.data() + L.off_hptr, L.tp.halo_ptr.data(), 8 * L.tp.halo_ptr.size());
             std::memcpy(host.data() + L.off_halo, L.tp.halo.data(), 4 * L.tp.halo.size());
-            std::memcpy(host.data() + L.off_nr1, L.tp.n_r1.data(), 4 * L.tp.n_r1.size());
-            std::memcpy(host.data() + L.off_lnbr, L.tp.lnbr.data(), 2 * L.tp.lnbr.size());
-            std::memcpy(host.data() + L.off_r1nbr, L.tp.r1nbr.data(), 2 * L.tp.r1nbr.size());
+            std::memcpy(host.data() + L.off_r1ptr, L.tp.r1_ptr.data(), 8 * L.tp.r1_ptr.size());
         }
     } catch (const std::bad_alloc&) {
         return fail(FVLBM_ERR_OOM, "fvlbm_init: out of host memory");
@@ -508,12 +619,9 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
     v.n_face = L.n_face;
     v.maxf = L.maxf;
     v.n_inst = M.n_inst;
+    v.desc = (const uint2*)(base + L.off_desc);
+    v.geo = base + L.off_geo;
     v.nbr = (const int32_t*)(base + L.off_nbr);
-    v.fid = (const int32_t*)(base + L.off_fid);
-    v.meta = (const uint32_t*)(base + L.off_meta);
-    v.cg = base + L.off_cg;
-    v.rv = base + L.off_rv;
-    v.nv = base + L.off_nv;
     v.area = (const double*)(base + L.off_area);
     v.grp = (const int32_t*)(base + L.off_grp);
     v.inst = (const InstParam*)(base + L.off_inst);
@@ -537,16 +645,16 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
     if (L.strategy == STRATEGY_TILE) {
         v.tile = L.tp.tile;
         v.n_tiles = L.tp.n_tiles;
-        v.lmax = L.tp.lmax;
-        v.gmax = L.tp.gmax;
-        v.r1max = L.tp.r1max;
+        v.tile_begin = (const int64_t*)(base + L.off_tbegin);
         v.halo_ptr = (const int64_t*)(base + L.off_hptr);
         v.halo = (const int32_t*)(base + L.off_halo);
-        v.n_r1 = (const int32_t*)(base + L.off_nr1);
-        v.lnbr = (const uint16_t*)(base + L.off_lnbr);
-        v.r1nbr = (const uint16_t*)(base + L.off_r1nbr);
-        v.rn = base + L.off_rn;
+        v.r1_ptr = (const int64_t*)(base + L.off_r1ptr);
+        v.r1link = (const uint32_t*)(base + L.off_r1link);
     }
+    s->pingpong = L.pingpong;
+    s->buf[0] = v.fa;
+    s->buf[1] = v.fb;
+    s->cur = 0;
 
     // Step 0 and the first residual snapshot
     rc = launch_init_eq(v, s->prec, s->stream);
@@ -569,8 +677,10 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
 
 extern "C" void fvlbm_solver_destroy(fvlbm_solver* s) {
     if (!s) return;
-    if (s->g1) cudaGraphExecDestroy(s->g1);
-    if (s->gk) cudaGraphExecDestroy(s->gk);
+    for (int b = 0; b < 2; b++) {
+        if (s->g1[b]) cudaGraphExecDestroy(s->g1[b]);
+        if (s->gk[b]) cudaGraphExecDestroy(s->gk[b]);
+    }
     if (s->own_ws && s->ws) {
         DeviceGuard dg(s->device);
         cudaStreamSynchronize(s->stream);
@@ -598,12 +708,28 @@ extern "C" int fvlbm_init(const fvlbm_mesh* mesh, const fvlbm_params* params, in
 // Stages per time step of each scheme.
 static int n_stages(int scheme) { return scheme == FVLBM_RK2 ? 2 : scheme == FVLBM_RK4 ? 4 : 1; }
 
+// Make buf[c] the current state (v.fa) and the other buffer v.fb.
+static void set_current(fvlbm_solver* s, int c) {
+    s->cur = c;
+    s->v.fa = s->buf[c];
+    s->v.fb = s->buf[c ^ 1];
+}
+
 // Enqueue one time step.  ev: null, or 3 events per stage (see launch_stage).
 static int enqueue_step(fvlbm_solver* s, void* const* ev = nullptr) {
     const DevView& v = s->v;
     switch (s->scheme) {
         case FVLBM_EULER:
-            return launch_stage(v, s->prec, s->stream, v.fa, v.fa, v.fa, 1.0, MODE_RK, ev);
+        case FVLBM_AB2: {
+            const int mode = s->scheme == FVLBM_EULER ? MODE_RK : (s->ab2_started ? MODE_AB2 : MODE_AB2_FIRST);
+            // in place on the two-kernel stage (each cell reads only its own state
+            // after the face values are written); fa -> fb and swap on the fused stage
+            int rc = launch_stage(v, s->prec, s->stream, v.fa, v.fa, s->pingpong ? v.fb : v.fa, 1.0, mode, ev);
+            if (rc) return rc;
+            if (s->scheme == FVLBM_AB2) s->ab2_started = true;
+            if (s->pingpong) set_current(s, s->cur ^ 1);
+            return FVLBM_OK;
+        }
         case FVLBM_RK2: {
             int rc = launch_stage(v, s->prec, s->stream, v.fa, v.fa, v.fb, 0.5, MODE_RK, ev);
             return rc ? rc : launch_stage(v, s->prec, s->stream, v.fb, v.fa, v.fa, 1.0, MODE_RK, ev ? ev + 3 : ev);
@@ -616,12 +742,6 @@ static int enqueue_step(fvlbm_solver* s, void* const* ev = nullptr) {
                 if (rc) return rc;
             }
             return FVLBM_OK;
-        }
-        case FVLBM_AB2: {
-            int rc = launch_stage(v, s->prec, s->stream, v.fa, v.fa, v.fa, 1.0,
-                                  s->ab2_started ? MODE_AB2 : MODE_AB2_FIRST, ev);
-            s->ab2_started = true;
-            return rc;
         }
     }
     return fail(FVLBM_ERR_ARG, "bad scheme");
@@ -677,7 +797,11 @@ extern "C" int fvlbm_launches_per_step(const fvlbm_solver* s, int64_t* launches)
 }
 
 // Capture `nsteps` steps of the solver's stream into an executable graph.
+// Capture only records launches: the host-side state (current buffer, AB2
+// start) is put back afterwards.
 static bool build_graph(fvlbm_solver* s, int64_t nsteps, cudaGraphExec_t* out) {
+    const int cur0 = s->cur;
+    const bool ab2 = s->ab2_started;
     if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
         return false;
@@ -686,6 +810,8 @@ static bool build_graph(fvlbm_solver* s, int64_t nsteps, cudaGraphExec_t* out) {
     for (int64_t k = 0; k < nsteps && rc == FVLBM_OK; k++) rc = enqueue_step(s);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+    set_current(s, cur0);
+    s->ab2_started = ab2;
     bool ok = rc == FVLBM_OK && e == cudaSuccess && g;
     if (ok) ok = cudaGraphInstantiate(out, g, 0) == cudaSuccess;
     if (g) cudaGraphDestroy(g);
@@ -700,7 +826,9 @@ static bool build_graph(fvlbm_solver* s, int64_t nsteps, cudaGraphExec_t* out) {
 // Steps are replayed from CUDA graphs (chunks of GRAPH_CHUNK, then single
 // steps) once the solver has run directly at least once (so that kernel
 // attributes are set outside capture) and AB2 has its history; the legacy
-// default stream cannot be captured and always launches directly.
+// default stream cannot be captured and always launches directly.  With a
+// ping-pong state there is one pair of graphs per starting buffer (a chunk
+// has an even number of steps and ends where it started).
 extern "C" int fvlbm_step(fvlbm_solver* s, int64_t n) {
     clear_error();
     if (!s || n < 0) return fail(FVLBM_ERR_ARG, "fvlbm_step: bad arguments");
@@ -709,27 +837,33 @@ extern "C" int fvlbm_step(fvlbm_solver* s, int64_t n) {
     cudaStreamIsCapturing(s->stream, &cs);
     bool graphs = s->graphs_ok && s->stream != nullptr && cs == cudaStreamCaptureStatusNone &&
                   s->direct_steps > 0 && (s->scheme != FVLBM_AB2 || s->ab2_started);
-    if (graphs && !s->g1) {
-        if (!build_graph(s, 1, &s->g1) || !build_graph(s, GRAPH_CHUNK, &s->gk)) {
+    auto ready = [&](int b) {
+        if (s->g1[b]) return true;
+        if (!build_graph(s, 1, &s->g1[b]) || !build_graph(s, GRAPH_CHUNK, &s->gk[b])) {
             s->graphs_ok = false;
-            graphs = false;
+            return false;
         }
-    }
-    while (graphs && n >= GRAPH_CHUNK) {
-        cudaError_t e = cudaGraphLaunch(s->gk, s->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "fvlbm_step: graph launch");
-        n -= GRAPH_CHUNK;
-    }
-    for (int64_t k = 0; k < n; k++) {
-        int rc;
+        return true;
+    };
+    while (n > 0) {
+        if (graphs && !ready(s->cur)) graphs = false;
+        int rc = FVLBM_OK;
+        if (graphs && n >= GRAPH_CHUNK) {
+            cudaError_t e = cudaGraphLaunch(s->gk[s->cur], s->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "fvlbm_step: graph launch");
+            n -= GRAPH_CHUNK;
+            continue;
+        }
         if (graphs) {
-            cudaError_t e = cudaGraphLaunch(s->g1, s->stream);
+            cudaError_t e = cudaGraphLaunch(s->g1[s->cur], s->stream);
             rc = e == cudaSuccess ? FVLBM_OK : cuda_fail(e, "fvlbm_step: graph launch");
+            if (rc == FVLBM_OK && s->pingpong) set_current(s, s->cur ^ 1);
         } else {
             rc = enqueue_step(s);
             s->direct_steps++;
         }
         if (rc) return rc;
+        n--;
     }
     return FVLBM_OK;
 }

@@ -34,317 +34,332 @@ __device__ __forceinline__ T bc_delta(uint32_t kind, const BcParam& b, int a, T 
     }
 }
 
+// Face value of direction a on a boundary face (Sec. 2.4.2): external outlet
+// f_i; inlet / outlet faces the cell flows out through: the reconstruction
+// f_i + grad f_i . r; otherwise the ghost value (half way for symmetry).
+template <typename T, bool DEV>
+__device__ __forceinline__ T boundary_face(uint32_t kind, bool out, const BcParam& b, int a, T fa, T rho, T ux, T uy,
+                                           T gxa, T gya, T rx, T ry, T nhx, T nhy) {
+    if (kind == SK_OUTLET && b.external) return fa;
+    if ((kind == SK_INLET || kind == SK_OUTLET) && out) return fa + gxa * rx + gya * ry;
+    const T d = bc_delta<T, DEV>(kind, b, a, fa, rho, ux, uy, feqs<T, DEV>(a, rho, ux, uy), nhx, nhy);
+    return kind == SK_SYMMETRY ? fa + T(0.5) * d : fa + d;
+}
+
 template <typename T>
 __device__ __forceinline__ bool finite_val(T x) { return isfinite(x); }
 
-// ------------------------------------------------------------------ kernels
-template <typename T, typename S, int MAXF, bool DEV>
-__global__ void __launch_bounds__(256) face_values_kernel(DevView v, const S* __restrict__ fin) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= v.n_cell) return;
-    const int64_t np = v.np;
-    const InstParam& P = v.inst[v.grp[i]];
-    const T* cg = (const T*)v.cg;
-    const T* rv = (const T*)v.rv;
-    const T* nv = (const T*)v.nv;
-    T* fv = (T*)v.fv;
-
-    T f[FVLBM_Q];
-    CellIO<S>::template load<T, DEV>(fin, i, np, P, f);
-    T rho, ux, uy;
-    moments<T, DEV>(f, rho, ux, uy);
-
-    // Step 2: gradient of f_1..f_8
-    T gx[FVLBM_Q - 1], gy[FVLBM_Q - 1];
+// Least-squares gradient (Eq. leastsquare) of f_1..f_8 of one cell from the
+// differences to its stencil values.  d: the cell's slot descriptors;
+// fnb(k, fj) fills fj[1..8] with the neighbour values across interior slot k.
+template <typename T, bool DEV, int MAXF, typename Nb>
+__device__ __forceinline__ void lsq_gradient(const uint2* d, const GeoRef<T, MAXF>& G, const BcParam* bcs, const T* f,
+                                             T rho, T ux, T uy, T* gx, T* gy, Nb fnb) {
 #pragma unroll
     for (int a = 0; a < FVLBM_Q - 1; a++) gx[a] = gy[a] = T(0);
 #pragma unroll
     for (int k = 0; k < MAXF; k++) {
-        const uint32_t meta = v.meta[k * np + i];
-        const uint32_t kind = meta & 0xFF;
+        const uint32_t kind = d[k].x & 0xFF;
         if (kind == SK_NONE) continue;
-        const T cx = cg[(0 * MAXF + k) * np + i], cy = cg[(1 * MAXF + k) * np + i];
+        const typename Vec2<T>::type c = G.cg(k);
         if (kind == SK_INTERIOR) {
-            const int64_t j = v.nbr[k * np + i];
             T fj[FVLBM_Q];
-            CellIO<S>::template load<T, DEV>(fin, j, np, v.inst[v.grp[j]], fj);
+            fnb(k, fj);
 #pragma unroll
             for (int a = 1; a < FVLBM_Q; a++) {
-                T d = fj[a] - f[a];
-                gx[a - 1] += cx * d;
-                gy[a - 1] += cy * d;
+                const T dd = fj[a] - f[a];
+                gx[a - 1] += c.x * dd;
+                gy[a - 1] += c.y * dd;
             }
         } else {
-            const BcParam& b = v.bc[meta >> 16];
-            T nx = nv[(0 * MAXF + k) * np + i], ny = nv[(1 * MAXF + k) * np + i];
-            T inv = T(1) / sqrt(nx * nx + ny * ny);
+            const BcParam& b = bcs[d[k].x >> 16];
+            const typename Vec2<T>::type n = G.nv(k);
+            const T inv = T(1) / sqrt(n.x * n.x + n.y * n.y);
 #pragma unroll
             for (int a = 1; a < FVLBM_Q; a++) {
-                T d = bc_delta<T, DEV>(kind, b, a, f[a], rho, ux, uy, feqs<T, DEV>(a, rho, ux, uy), nx * inv, ny * inv);
-                gx[a - 1] += cx * d;
-                gy[a - 1] += cy * d;
-            }
-        }
-    }
-
-    // Steps 1, 3: face values written by their upwind cell; boundary faces in full
-#pragma unroll
-    for (int k = 0; k < MAXF; k++) {
-        const uint32_t meta = v.meta[k * np + i];
-        const uint32_t kind = meta & 0xFF;
-        if (kind == SK_NONE) continue;
-        const uint32_t mask = (meta >> 8) & 0xFF;
-        const int64_t fid = v.fid[k * np + i];
-        const T rx = rv[(0 * MAXF + k) * np + i], ry = rv[(1 * MAXF + k) * np + i];
-        if (kind == SK_INTERIOR) {
-#pragma unroll
-            for (int a = 1; a < FVLBM_Q; a++)
-                if (mask & (1u << (a - 1))) fv[(a - 1) * v.n_face + fid] = f[a] + gx[a - 1] * rx + gy[a - 1] * ry;
-        } else {
-            const BcParam& b = v.bc[meta >> 16];
-            T nx = nv[(0 * MAXF + k) * np + i], ny = nv[(1 * MAXF + k) * np + i];
-            T inv = T(1) / sqrt(nx * nx + ny * ny);
-#pragma unroll
-            for (int a = 1; a < FVLBM_Q; a++) {
-                const bool out = (mask >> (a - 1)) & 1u;
-                T val;
-                if (kind == SK_OUTLET && b.external) {
-                    val = f[a];
-                } else if ((kind == SK_INLET || kind == SK_OUTLET) && out) {
-                    val = f[a] + gx[a - 1] * rx + gy[a - 1] * ry;
-                } else {
-                    T d = bc_delta<T, DEV>(kind, b, a, f[a], rho, ux, uy, feqs<T, DEV>(a, rho, ux, uy), nx * inv, ny * inv);
-                    val = kind == SK_SYMMETRY ? f[a] + T(0.5) * d : f[a] + d;
-                }
-                fv[(a - 1) * v.n_face + fid] = val;
+                const T dd = bc_delta<T, DEV>(kind, b, a, f[a], rho, ux, uy, feqs<T, DEV>(a, rho, ux, uy), n.x * inv,
+                                              n.y * inv);
+                gx[a - 1] += c.x * dd;
+                gy[a - 1] += c.y * dd;
             }
         }
     }
 }
 
+// Values of one cell on its faces (Eq. lslrflux, Sec. 2.4.2) into a face
+// table with direction stride `stride`: on interior faces the directions in
+// the slot's writer mask, on boundary faces every direction.  face(k) is the
+// slot's row in the table, or null to skip the slot.
+template <typename T, bool DEV, int MAXF, typename Row>
+__device__ __forceinline__ void write_faces(const uint2* d, const GeoRef<T, MAXF>& G, const BcParam* bcs, const T* f,
+                                            T rho, T ux, T uy, const T* gx, const T* gy, int64_t stride, Row face) {
+#pragma unroll
+    for (int k = 0; k < MAXF; k++) {
+        const uint32_t kind = d[k].x & 0xFF;
+        if (kind == SK_NONE) continue;
+        T* fo = face(k);
+        if (!fo) continue;
+        const uint32_t mask = (d[k].x >> 8) & 0xFF;
+        const typename Vec2<T>::type r = G.rv(k);
+        if (kind == SK_INTERIOR) {
+#pragma unroll
+            for (int a = 1; a < FVLBM_Q; a++)
+                if (mask & (1u << (a - 1))) fo[(a - 1) * stride] = f[a] + gx[a - 1] * r.x + gy[a - 1] * r.y;
+        } else {
+            const BcParam& b = bcs[d[k].x >> 16];
+            const typename Vec2<T>::type n = G.nv(k);
+            const T inv = T(1) / sqrt(n.x * n.x + n.y * n.y);
+#pragma unroll
+            for (int a = 1; a < FVLBM_Q; a++)
+                fo[(a - 1) * stride] = boundary_face<T, DEV>(kind, (mask >> (a - 1)) & 1u, b, a, f[a], rho, ux, uy,
+                                                             gx[a - 1], gy[a - 1], r.x, r.y, n.x * inv, n.y * inv);
+        }
+    }
+}
+
+// Flux sum of Eq. (rhs) from a face table: sum over the slots of
+// (e_a . n dl / A) f_face (deviation mode: of f_face - f_a, the same in exact
+// arithmetic because the face vectors of a closed cell sum to zero, without
+// the rounding of the FP32 face vectors acting on the constant part of g).
+template <typename T, bool DEV, int MAXF, typename Row>
+__device__ __forceinline__ void flux_sum(const uint2* d, const typename Vec2<T>::type* n, const T* f, int64_t stride,
+                                         T* flux, Row face) {
+#pragma unroll
+    for (int a = 0; a < FVLBM_Q; a++) flux[a] = T(0);
+#pragma unroll
+    for (int k = 0; k < MAXF; k++) {
+        if ((d[k].x & 0xFF) == SK_NONE) continue;
+        const T* fi = face(k);
+#pragma unroll
+        for (int a = 1; a < FVLBM_Q; a++) {
+            const T en = T(EXA(a)) * n[k].x + T(EYA(a)) * n[k].y;
+            const T fa = fi[(a - 1) * stride];
+            flux[a] += en * (DEV ? fa - f[a] : fa);
+        }
+    }
+}
+
+// cp.async copy of one 4- or 8-byte element from global to shared memory.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Collision and time update of one cell (Eq. rhs, Sec. 2.3): rhs = -flux -
+// (f - f^eq) / tau, then out = base + beta dt rhs (multistage; fb the base
+// state, or null when it is f itself) or the AB2 combination.  Returns false
+// when an output is not finite.
+template <typename T, typename S, bool DEV>
+__device__ __forceinline__ bool update_cell(const DevView& v, const InstParam& P, int64_t i, const T* f, T rho, T ux,
+                                            T uy, const T* flux, const T* fb, S* fout, T beta, int mode) {
+    const T inv_tau = inst_inv_tau<T>(P);
+    const T dt = inst_dt<T>(P);
+    bool bad = false;
+    T* rp = (T*)v.rprev;
+    T out[FVLBM_Q];
+#pragma unroll
+    for (int a = 0; a < FVLBM_Q; a++) {
+        const T rhs = -flux[a] - (f[a] - feqs<T, DEV>(a, rho, ux, uy)) * inv_tau;
+        if (mode == MODE_RK) {
+            out[a] = (fb ? fb[a] : f[a]) + beta * dt * rhs;
+        } else if (mode == MODE_AB2_FIRST) {
+            out[a] = f[a] + dt * rhs;
+            rp[a * v.np + i] = rhs;
+        } else {
+            out[a] = f[a] + dt * (T(1.5) * rhs - T(0.5) * rp[a * v.np + i]);
+            rp[a * v.np + i] = rhs;
+        }
+        bad |= !finite_val(out[a]);
+    }
+    CellIO<S>::template store<T, DEV>(fout, i, P, out);
+    return !bad;
+}
+
+// ------------------------------------------------------------------ kernels
+// Two-kernel stage, kernel 1 (Steps 1-3): per cell the gradient, then the
+// value of every (face, direction) it is the upwind side of, and every
+// direction of its boundary faces, into the face table (one writer each).
+template <typename T, typename S, int MAXF, bool DEV>
+__global__ void __launch_bounds__(256) face_values_kernel(DevView v, const S* __restrict__ fin) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= v.n_cell) return;
+    const GeoRef<T, MAXF> G(v.desc, v.geo, i);
+    const int32_t* nb = v.nbr + blk_index(i, MAXF);
+    uint2 d[MAXF];
+#pragma unroll
+    for (int k = 0; k < MAXF; k++) d[k] = G.desc(k);
+    T f[FVLBM_Q];
+    CellIO<S>::template load<T, DEV>(fin, i, v.inst[v.grp[i]], f);
+    T rho, ux, uy;
+    moments<T, DEV>(f, rho, ux, uy);
+    T gx[FVLBM_Q - 1], gy[FVLBM_Q - 1];
+    lsq_gradient<T, DEV, MAXF>(d, G, v.bc, f, rho, ux, uy, gx, gy, [&](int k, T* fj) {
+        const int64_t j = nb[k * BLK];
+        CellIO<S>::template load<T, DEV>(fin, j, v.inst[v.grp[j]], fj);
+    });
+    T* fv = (T*)v.fv;
+    write_faces<T, DEV, MAXF>(d, G, v.bc, f, rho, ux, uy, gx, gy, v.n_face, [&](int k) { return fv + d[k].y; });
+}
+
+// Two-kernel stage, kernel 2 (Steps 4-5): flux sum over the cell's faces,
+// collision and time update.
 template <typename T, typename S, int MAXF, bool DEV>
 __global__ void __launch_bounds__(256) update_kernel(DevView v, const S* __restrict__ fin, const S* fbase, S* fout,
                                                      T beta, int mode) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.n_cell) return;
-    const int64_t np = v.np;
     const InstParam& P = v.inst[v.grp[i]];
-    const T* nv = (const T*)v.nv;
-    const T* fv = (const T*)v.fv;
-
-    T f[FVLBM_Q];
-    CellIO<S>::template load<T, DEV>(fin, i, np, P, f);
-    T rho, ux, uy;
-    moments<T, DEV>(f, rho, ux, uy);
-
-    T flux[FVLBM_Q];
-#pragma unroll
-    for (int a = 0; a < FVLBM_Q; a++) flux[a] = T(0);
+    const GeoRef<T, MAXF> G(v.desc, v.geo, i);
+    uint2 d[MAXF];
+    typename Vec2<T>::type n[MAXF];
 #pragma unroll
     for (int k = 0; k < MAXF; k++) {
-        const uint32_t kind = v.meta[k * np + i] & 0xFF;
-        if (kind == SK_NONE) continue;
-        const int64_t fid = v.fid[k * np + i];
-        const T nx = nv[(0 * MAXF + k) * np + i], ny = nv[(1 * MAXF + k) * np + i];
-#pragma unroll
-        for (int a = 1; a < FVLBM_Q; a++) {
-            const T en = T(EXA(a)) * nx + T(EYA(a)) * ny;
-            // deviation mode: the face vectors of a closed cell sum to zero, so
-            // subtracting the cell value leaves the flux unchanged in exact
-            // arithmetic and removes the rounding of the FP32 face vectors
-            // from the constant part of g
-            const T face = fv[(a - 1) * v.n_face + fid];
-            flux[a] += en * (DEV ? face - f[a] : face);
-        }
+        d[k] = G.desc(k);
+        n[k] = G.nv(k);
     }
-    const T inv_tau = inst_inv_tau<T>(P);
-    const T dt = inst_dt<T>(P);
-    bool bad = false;
-    T* rp = (T*)v.rprev;
-    T fb[FVLBM_Q], out[FVLBM_Q];
-    if (mode == MODE_RK && fbase != fin) CellIO<S>::template load<T, DEV>(fbase, i, np, P, fb);
-#pragma unroll
-    for (int a = 0; a < FVLBM_Q; a++) {
-        const T rhs = -flux[a] - (f[a] - feqs<T, DEV>(a, rho, ux, uy)) * inv_tau;
-        if (mode == MODE_RK) {
-            out[a] = (fbase == fin ? f[a] : fb[a]) + beta * dt * rhs;
-        } else if (mode == MODE_AB2_FIRST) {
-            out[a] = f[a] + dt * rhs;
-            rp[a * np + i] = rhs;
-        } else {
-            out[a] = f[a] + dt * (T(1.5) * rhs - T(0.5) * rp[a * np + i]);
-            rp[a * np + i] = rhs;
-        }
-        bad |= !finite_val(out[a]);
-    }
-    CellIO<S>::template store<T, DEV>(fout, i, np, P, out);
-    if (bad) *v.flag = 1;
+    T f[FVLBM_Q];
+    CellIO<S>::template load<T, DEV>(fin, i, P, f);
+    T rho, ux, uy;
+    moments<T, DEV>(f, rho, ux, uy);
+    T flux[FVLBM_Q];
+    const T* fv = (const T*)v.fv;
+    flux_sum<T, DEV, MAXF>(d, n, f, v.n_face, flux, [&](int k) { return fv + d[k].y; });
+    T fb[FVLBM_Q];
+    const bool rk_base = mode == MODE_RK && fbase != fin;
+    if (rk_base) CellIO<S>::template load<T, DEV>(fbase, i, P, fb);
+    if (!update_cell<T, S, DEV>(v, P, i, f, rho, ux, uy, flux, rk_base ? fb : nullptr, fout, beta, mode))
+        *v.flag = 1;
 }
 
-// Fused stage: one CTA per tile of TILE consecutive cells (Hilbert order).
-//   phase 1  f of the tile, its 1-ring and its 2-ring into shared memory
-//   phase 2  gradients (Eq. leastsquare) of the tile and 1-ring cells, kept in
-//            shared memory
-//   phase 3  per tile cell: face values (Eq. lslrflux / Sec. 2.4.2) from the
-//            upwind side -- its own gradient, or the neighbour's from shared
-//            memory -- flux sum, collision and time update (Eq. rhs, Sec. 2.3)
-// Each face value is evaluated by both cells of the face from the same data,
-// so no face-value array goes through memory.
+// Fused stage: one CTA per tile of at most TILE consecutive cells (Hilbert
+// order), everything between the state read and the state write in shared
+// memory:
+//   phase 1  f of the tile, its 1-ring and its 2-ring (cp.async when the
+//            stored type is the arithmetic type)
+//   phase 2  per tile and 1-ring cell: the gradient (Eq. leastsquare), then
+//            its values on the tile's faces (Eq. lslrflux / Sec. 2.4.2): on
+//            interior faces the directions it writes (upwind side), on
+//            boundary faces (tile cells) every direction -- one writer per
+//            (face, direction), into a table of the tile's faces
+//   phase 3  per tile cell: flux sum from the face table, collision and the
+//            time update (Eq. rhs, Sec. 2.3)
+// The global loads of each phase are issued before the barrier that precedes
+// it, so that their latency overlaps the wait.  Shared-memory strides are
+// compile-time constants (TileDims); the planner keeps every tile within them.
 template <typename T, typename S, int MAXF, bool DEV, int TILE>
-__global__ void __launch_bounds__(TILE) stage_tile_kernel(DevView v, const S* __restrict__ fin,
+__global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0 ? (sizeof(T) == 4 ? 1024 : 512) / TILE : 1)
+    stage_tile_kernel(DevView v, const S* __restrict__ fin,
                                                           const S* fbase, S* fout, T beta, int mode) {
+    constexpr int LS = TileDims<TILE, MAXF>::LS;
+    constexpr int FS = TileDims<TILE, MAXF>::FS;
+    typedef typename Vec2<T>::type T2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lmax = v.lmax, gmax = v.gmax;
-    T* fs = (T*)smem_raw;            // [9][lmax]
-    T* gxs = fs + FVLBM_Q * lmax;    // [8][gmax]
-    T* gys = gxs + (FVLBM_Q - 1) * gmax;
-    const int64_t np = v.np;
+    T* fs = (T*)smem_raw;            // [9][LS]  f of the local cells
+    T* fvs = fs + FVLBM_Q * LS;      // [8][FS]  face values of directions 1..8
     const int64_t t = blockIdx.x;
-    const int64_t c0 = t * TILE;
-    const int nt = (int)min((int64_t)TILE, v.n_cell - c0);
+    const int64_t c0 = v.tile_begin[t];
+    const int nt = (int)(v.tile_begin[t + 1] - c0);
     const int64_t h0 = v.halo_ptr[t];
     const int nh = (int)(v.halo_ptr[t + 1] - h0);
-    const int n1 = v.n_r1[t];
-    const int nl = nt + nh;
-    const T* cg = (const T*)v.cg;
-    const T* rv = (const T*)v.rv;
-    const T* rn = (const T*)v.rn;
-    const T* nv = (const T*)v.nv;
+    const int64_t q0 = v.r1_ptr[t];
+    const int n1 = (int)(v.r1_ptr[t + 1] - q0);
+    const int l = threadIdx.x;
+    const bool mine = l < nt;          // this thread owns tile cell l
+    const int64_t gi = c0 + l;
 
     // phase 1
-    for (int l = threadIdx.x; l < nl; l += TILE) {
-        const int64_t gi = l < nt ? c0 + l : (int64_t)v.halo[h0 + l - nt];
-        T f[FVLBM_Q];
-        CellIO<S>::template load<T, DEV>(fin, gi, np, v.inst[v.grp[gi]], f);
+    for (int x = l; x < nt + nh; x += TILE) {
+        const int64_t gx = x < nt ? c0 + x : (int64_t)v.halo[h0 + (x - nt)];
+        if constexpr (sizeof(S) == sizeof(T)) {
+            const S* p = fin + blk_index(gx, FVLBM_Q);
 #pragma unroll
-        for (int a = 0; a < FVLBM_Q; a++) fs[a * lmax + l] = f[a];
+            for (int a = 0; a < FVLBM_Q; a++) cp_async_elem<T>(fs + a * LS + x, (const T*)p + a * BLK);
+        } else {
+            T f[FVLBM_Q];
+            CellIO<S>::template load<T, DEV>(fin, gx, v.inst[v.grp[gx]], f);
+#pragma unroll
+            for (int a = 0; a < FVLBM_Q; a++) fs[a * LS + x] = f[a];
+        }
     }
+    // phase 2 geometry of the own cell, in flight during the wait
+    const GeoRef<T, MAXF> G(v.desc, v.geo, mine ? gi : c0);
+    uint2 d[MAXF];
+#pragma unroll
+    for (int k = 0; k < MAXF; k++) d[k] = mine ? G.desc(k) : make_uint2(SK_NONE, 0xFFFFFFFFu);
+    if constexpr (sizeof(S) == sizeof(T)) cp_async_wait_all();
     __syncthreads();
 
-    // phase 2
-    for (int l = threadIdx.x; l < nt + n1; l += TILE) {
-        const bool own = l < nt;
-        const int64_t gi = own ? c0 + l : (int64_t)v.halo[h0 + l - nt];
+    // phase 2: the own tile cell, then 1-ring entries
+    if (mine) {
         T f[FVLBM_Q];
 #pragma unroll
-        for (int a = 0; a < FVLBM_Q; a++) f[a] = fs[a * lmax + l];
+        for (int a = 0; a < FVLBM_Q; a++) f[a] = fs[a * LS + l];
         T rho, ux, uy;
         moments<T, DEV>(f, rho, ux, uy);
         T gx[FVLBM_Q - 1], gy[FVLBM_Q - 1];
+        lsq_gradient<T, DEV, MAXF>(d, G, v.bc, f, rho, ux, uy, gx, gy, [&](int k, T* fj) {
+            const T* p = fs + (d[k].y & 0xFFFF);
 #pragma unroll
-        for (int a = 0; a < FVLBM_Q - 1; a++) gx[a] = gy[a] = T(0);
+            for (int a = 1; a < FVLBM_Q; a++) fj[a] = p[a * LS];
+        });
+        write_faces<T, DEV, MAXF>(d, G, v.bc, f, rho, ux, uy, gx, gy, FS, [&](int k) { return fvs + (d[k].y >> 16); });
+    }
+    for (int e = l; e < n1; e += TILE) {
+        const int x = nt + e;
+        const int64_t gj = v.halo[h0 + e];
+        const GeoRef<T, MAXF> H(v.desc, v.geo, gj);
+        const uint32_t* rl = v.r1link + blk_index(q0 + e, MAXF);
+        uint2 dj[MAXF];
 #pragma unroll
         for (int k = 0; k < MAXF; k++) {
-            const uint32_t meta = v.meta[k * np + gi];
-            const uint32_t kind = meta & 0xFF;
-            if (kind == SK_NONE) continue;
-            const T cx = cg[(0 * MAXF + k) * np + gi], cy = cg[(1 * MAXF + k) * np + gi];
-            if (kind == SK_INTERIOR) {
-                const int lj = own ? (int)v.lnbr[k * np + gi] : (int)v.r1nbr[(h0 + l - nt) * MAXF + k];
-#pragma unroll
-                for (int a = 1; a < FVLBM_Q; a++) {
-                    const T d = fs[a * lmax + lj] - f[a];
-                    gx[a - 1] += cx * d;
-                    gy[a - 1] += cy * d;
-                }
-            } else {
-                const BcParam& b = v.bc[meta >> 16];
-                const T nx = nv[(0 * MAXF + k) * np + gi], ny = nv[(1 * MAXF + k) * np + gi];
-                const T inv = T(1) / sqrt(nx * nx + ny * ny);
-#pragma unroll
-                for (int a = 1; a < FVLBM_Q; a++) {
-                    const T d = bc_delta<T, DEV>(kind, b, a, f[a], rho, ux, uy, feqs<T, DEV>(a, rho, ux, uy),
-                                                 nx * inv, ny * inv);
-                    gx[a - 1] += cx * d;
-                    gy[a - 1] += cy * d;
-                }
-            }
+            dj[k] = H.desc(k);
+            dj[k].y = rl[k * BLK];   // local links of the 1-ring entry
         }
+        T f[FVLBM_Q];
 #pragma unroll
-        for (int a = 0; a < FVLBM_Q - 1; a++) {
-            gxs[a * gmax + l] = gx[a];
-            gys[a * gmax + l] = gy[a];
-        }
+        for (int a = 0; a < FVLBM_Q; a++) f[a] = fs[a * LS + x];
+        T rho, ux, uy;
+        moments<T, DEV>(f, rho, ux, uy);
+        T gx[FVLBM_Q - 1], gy[FVLBM_Q - 1];
+        lsq_gradient<T, DEV, MAXF>(dj, H, v.bc, f, rho, ux, uy, gx, gy, [&](int k, T* fj) {
+            const T* p = fs + (dj[k].y & 0xFFFF);
+#pragma unroll
+            for (int a = 1; a < FVLBM_Q; a++) fj[a] = p[a * LS];
+        });
+        // only faces shared with the tile; the 1-ring's boundary faces are not needed
+        write_faces<T, DEV, MAXF>(dj, H, v.bc, f, rho, ux, uy, gx, gy, FS, [&](int k) {
+            const uint32_t lf = dj[k].y >> 16;
+            return (lf == LINK_NONE || (dj[k].x & 0xFF) != SK_INTERIOR) ? (T*)nullptr : fvs + lf;
+        });
+    }
+    // phase 3 inputs, in flight during the wait
+    T2 n[MAXF];
+    T fb[FVLBM_Q];
+    const bool rk_base = mode == MODE_RK && fbase != fin;
+    if (mine) {
+#pragma unroll
+        for (int k = 0; k < MAXF; k++) n[k] = G.nv(k);
+        if (rk_base) CellIO<S>::template load<T, DEV>(fbase, gi, v.inst[v.grp[gi]], fb);
     }
     __syncthreads();
 
     // phase 3
-    const int l = threadIdx.x;
-    if (l >= nt) return;
-    const int64_t gi = c0 + l;
+    if (!mine) return;
     const InstParam& P = v.inst[v.grp[gi]];
     T f[FVLBM_Q];
 #pragma unroll
-    for (int a = 0; a < FVLBM_Q; a++) f[a] = fs[a * lmax + l];
+    for (int a = 0; a < FVLBM_Q; a++) f[a] = fs[a * LS + l];
     T rho, ux, uy;
     moments<T, DEV>(f, rho, ux, uy);
     T flux[FVLBM_Q];
-#pragma unroll
-    for (int a = 0; a < FVLBM_Q; a++) flux[a] = T(0);
-#pragma unroll
-    for (int k = 0; k < MAXF; k++) {
-        const uint32_t meta = v.meta[k * np + gi];
-        const uint32_t kind = meta & 0xFF;
-        if (kind == SK_NONE) continue;
-        const uint32_t mask = (meta >> 8) & 0xFF;
-        const T nx = nv[(0 * MAXF + k) * np + gi], ny = nv[(1 * MAXF + k) * np + gi];
-        const T rx = rv[(0 * MAXF + k) * np + gi], ry = rv[(1 * MAXF + k) * np + gi];
-        if (kind == SK_INTERIOR) {
-            const int lj = (int)v.lnbr[k * np + gi];
-            const T sx = rn[(0 * MAXF + k) * np + gi], sy = rn[(1 * MAXF + k) * np + gi];
-#pragma unroll
-            for (int a = 1; a < FVLBM_Q; a++) {
-                const T en = T(EXA(a)) * nx + T(EYA(a)) * ny;
-                T face;
-                if (mask & (1u << (a - 1)))
-                    face = f[a] + gxs[(a - 1) * gmax + l] * rx + gys[(a - 1) * gmax + l] * ry;
-                else
-                    face = fs[a * lmax + lj] + gxs[(a - 1) * gmax + lj] * sx + gys[(a - 1) * gmax + lj] * sy;
-                flux[a] += en * (DEV ? face - f[a] : face);
-            }
-        } else {
-            const BcParam& b = v.bc[meta >> 16];
-            const T inv = T(1) / sqrt(nx * nx + ny * ny);
-#pragma unroll
-            for (int a = 1; a < FVLBM_Q; a++) {
-                const bool out = (mask >> (a - 1)) & 1u;
-                T face;
-                if (kind == SK_OUTLET && b.external) {
-                    face = f[a];
-                } else if ((kind == SK_INLET || kind == SK_OUTLET) && out) {
-                    face = f[a] + gxs[(a - 1) * gmax + l] * rx + gys[(a - 1) * gmax + l] * ry;
-                } else {
-                    const T d = bc_delta<T, DEV>(kind, b, a, f[a], rho, ux, uy, feqs<T, DEV>(a, rho, ux, uy),
-                                                 nx * inv, ny * inv);
-                    face = kind == SK_SYMMETRY ? f[a] + T(0.5) * d : f[a] + d;
-                }
-                const T en = T(EXA(a)) * nx + T(EYA(a)) * ny;
-                flux[a] += en * (DEV ? face - f[a] : face);
-            }
-        }
-    }
-    const T inv_tau = inst_inv_tau<T>(P);
-    const T dt = inst_dt<T>(P);
-    bool bad = false;
-    T* rp = (T*)v.rprev;
-    T fb[FVLBM_Q], outv[FVLBM_Q];
-    if (mode == MODE_RK && fbase != fin) CellIO<S>::template load<T, DEV>(fbase, gi, np, P, fb);
-#pragma unroll
-    for (int a = 0; a < FVLBM_Q; a++) {
-        const T rhs = -flux[a] - (f[a] - feqs<T, DEV>(a, rho, ux, uy)) * inv_tau;
-        if (mode == MODE_RK) {
-            outv[a] = (fbase == fin ? f[a] : fb[a]) + beta * dt * rhs;
-        } else if (mode == MODE_AB2_FIRST) {
-            outv[a] = f[a] + dt * rhs;
-            rp[a * np + gi] = rhs;
-        } else {
-            outv[a] = f[a] + dt * (T(1.5) * rhs - T(0.5) * rp[a * np + gi]);
-            rp[a * np + gi] = rhs;
-        }
-        bad |= !finite_val(outv[a]);
-    }
-    CellIO<S>::template store<T, DEV>(fout, gi, np, P, outv);
-    if (bad) *v.flag = 1;
+    flux_sum<T, DEV, MAXF>(d, n, f, FS, flux, [&](int k) { return fvs + (d[k].y >> 16); });
+    if (!update_cell<T, S, DEV>(v, P, gi, f, rho, ux, uy, flux, rk_base ? fb : nullptr, fout, beta, mode))
+        *v.flag = 1;
 }
 
 
@@ -360,7 +375,7 @@ template <typename T, typename S, int MAXF, bool DEV, int TILE>
 static int tile_launch(const DevView& v, cudaStream_t st, const void* fin, const void* fbase, void* fout,
                        double beta, int mode) {
     auto kern = stage_tile_kernel<T, S, MAXF, DEV, TILE>;
-    const size_t smem = tile_smem_bytes(v, sizeof(T));
+    const size_t smem = tile_smem_bytes_for(TileDims<TILE, MAXF>::LS, TileDims<TILE, MAXF>::FS, (int)sizeof(T));
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return fail(FVLBM_ERR_CUDA, "fused stage: %zu B shared memory: %s", smem, cudaGetErrorString(e));
@@ -376,7 +391,9 @@ static int tile_dispatch(const DevView& v, cudaStream_t st, const void* fin, con
         case 128: return tile_launch<T, S, MAXF, DEV, 128>(v, st, fin, fbase, fout, beta, mode);
         case 256: return tile_launch<T, S, MAXF, DEV, 256>(v, st, fin, fbase, fout, beta, mode);
         case 512: return tile_launch<T, S, MAXF, DEV, 512>(v, st, fin, fbase, fout, beta, mode);
-        case 1024: return tile_launch<T, S, MAXF, DEV, 1024>(v, st, fin, fbase, fout, beta, mode);
+        case 1024:   // FP64 tiles of 1024 cells do not fit in shared memory; the planner never makes them
+            if constexpr (sizeof(T) == 4) return tile_launch<T, S, MAXF, DEV, 1024>(v, st, fin, fbase, fout, beta, mode);
+            break;
     }
     return fail(FVLBM_ERR_ARG, "unsupported tile size %d", v.tile);
 }

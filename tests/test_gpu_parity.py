@@ -96,17 +96,57 @@ def test_stage_kernel_variants(fv, orc, name, kernel):
     o = orc.Oracle(m)
     dt = o.cfl_dt(0.5, 0.1, tau, "rk2")
     f0 = f_random(orc, m, seed=17)
-    s = fv.Solver(fv.Mesh(m), fv.make_params(tau, dt=dt, scheme="rk2", precision="fp64", kernel=kernel))
-    s.set_f(f0)
-    s.step(15)
-    o.set_f(f0)
-    o.run("rk2", tau, dt, 15)
-    assert rel_err(s.get_f(), o.get_f()) < FP64_TOL
+    if kernel == 1024:
+        # FP64 tiles of 1024 cells need more shared memory than a CTA has
+        with pytest.raises(fv.FvlbmError) as e:
+            fv.Solver(fv.Mesh(m), fv.make_params(tau, dt=dt, scheme="rk2", precision="fp64", kernel=kernel))
+        assert e.value.name == "UNSUPPORTED"
+    else:
+        s = fv.Solver(fv.Mesh(m), fv.make_params(tau, dt=dt, scheme="rk2", precision="fp64", kernel=kernel))
+        s.set_f(f0)
+        s.step(15)
+        o.set_f(f0)
+        o.run("rk2", tau, dt, 15)
+        assert rel_err(s.get_f(), o.get_f()) < FP64_TOL
     ref = fv.Solver(fv.Mesh(m), fv.make_params(tau, dt=dt, scheme="rk2", precision="fp32", kernel=1))
     got = fv.Solver(fv.Mesh(m), fv.make_params(tau, dt=dt, scheme="rk2", precision="fp32", kernel=kernel))
     for x in (ref, got):
         x.set_f(f0)
         x.step(15)
+    assert rel_err(got.get_f(), ref.get_f()) < 1e-6
+
+
+@pytest.mark.parametrize("kernel", [128, 512])
+@pytest.mark.parametrize("scheme", ["euler", "ab2", "rk4"])
+@pytest.mark.parametrize("name", ["cylinder", "bricks", "internal_io", "symmetry", "two_tri_periodic", "far_field"])
+def test_fused_stage_every_scheme(fv, orc, name, scheme, kernel):
+    """Fused stage in FP64 against the oracle for every time scheme: the
+    single-stage schemes alternate the state between two buffers; step counts
+    mix graph chunks (32 steps) and single steps from either buffer."""
+    m = MESHES[name]()
+    tau = 0.15
+    o = orc.Oracle(m)
+    dt = o.cfl_dt(0.5, 0.1, tau, scheme)
+    f0 = f_random(orc, m, seed=23)
+    s = fv.Solver(fv.Mesh(m), fv.make_params(tau, dt=dt, scheme=scheme, precision="fp64", kernel=kernel))
+    s.set_f(f0)
+    for n in (1, 33, 2, 1):
+        s.step(n)
+    o.set_f(f0)
+    o.run(scheme, tau, dt, 37)
+    assert rel_err(s.get_f(), o.get_f()) < FP64_TOL
+
+
+@pytest.mark.parametrize("scheme", ["euler", "ab2"])
+def test_fused_single_stage_many_tiles(fv, scheme):
+    """A mesh with many more tiles than resident CTAs: the fused stage of a
+    single-stage scheme (ping-pong state) agrees with the two-kernel stage."""
+    m = mg.cavity(500, 8.0)   # 250,000 cells: ~1950 tiles of 128, more than fit on the GPU at once
+    p = dict(scheme=scheme, precision="fp32", u0=(0.0, 0.0))
+    ref = fv.Solver(fv.Mesh(m), fv.make_params(0.05, kernel=1, **p))
+    got = fv.Solver(fv.Mesh(m), fv.make_params(0.05, kernel=128, **p))
+    for x in (ref, got):
+        x.step(41)
     assert rel_err(got.get_f(), ref.get_f()) < 1e-6
 
 
@@ -281,12 +321,13 @@ def test_edge_cases(fv, orc):
     assert e.value.name == "DIVERGED"
 
 
+@pytest.mark.parametrize("kernel", [1, 128])
 @pytest.mark.parametrize("scheme", ["rk2", "ab2", "euler"])
-def test_graph_replay_matches_direct_launches(fv, scheme):
+def test_graph_replay_matches_direct_launches(fv, scheme, kernel):
     """fvlbm_step replays CUDA graphs of 32 steps and of 1 step; the state is
     bitwise the same as with one step per call, also across an AB2 restart."""
     m = mg.cylinder_hybrid(n_rad=8, n_circ=32, first=0.02, growth=1.15, r_far=8.0, n_tri_rings=8, seed=4)
-    p = fv.make_params(0.02, scheme=scheme, precision="fp32", u0=(0.05, 0.0))
+    p = fv.make_params(0.02, scheme=scheme, precision="fp32", u0=(0.05, 0.0), kernel=kernel)
     a, b = fv.Solver(fv.Mesh(m), p), fv.Solver(fv.Mesh(m), p)
     for _ in range(70):
         a.step(1)
