@@ -85,14 +85,17 @@ struct BcParam {
 constexpr int BLK_SHIFT = 5;
 constexpr int BLK = 1 << BLK_SHIFT;
 
-// Fused stage: shared-memory capacity of a tile of TILE cells (compile-time
+// Fused stage: shared-memory capacity of a tile of TILE threads (compile-time
 // strides, so that every shared-memory access is a fixed offset from one
-// index): LS local cells (tile, 1-ring, 2-ring) and FS local faces (the faces
-// of the tile's cells).  The tile planner ends a tile early when its halo or
-// faces would not fit.
-template <int TILE, int MAXF> struct TileDims {
-    static constexpr int LS = 2 * TILE + 128;
-    static constexpr int FS = MAXF <= 4 ? (5 * TILE) / 2 : 4 * TILE;
+// index): LS local cells (tile, 1-ring, 2-ring), FS local faces (the faces of
+// the tile's cells) and, for the cell each thread computes a gradient for, its
+// least-squares and reconstruction vectors (2 MAXF pairs of reals of RSIZE
+// bytes).  The tile planner ends a tile early when it would not fit.
+template <int TILE, int MAXF, int RSIZE> struct TileDims {
+    static constexpr int LS = (3 * TILE) / 2 + 64;
+    static constexpr int FS = MAXF <= 4 ? 2 * TILE : (7 * TILE) / 2;
+    static constexpr size_t BYTES =
+        (size_t)RSIZE * ((size_t)FVLBM_Q * LS + (size_t)(FVLBM_Q - 1) * FS + (size_t)4 * MAXF * TILE);
 };
 // "no local face / neighbour" in a 16-bit link field
 constexpr uint32_t LINK_NONE = 0xFFFF;
@@ -118,7 +121,7 @@ struct DevView {
     void* fa;   // S blocked [9] (or the split format): the state
     void* fb;   // same: stage state (multistage schemes) or the other buffer of a ping-pong pair
     void* rprev;// T [9][np]  AB2 previous RHS
-    void* fv;   // T [8][n_face] face values of directions 1..8
+    void* fv;   // T [8][n_face] face values of directions 1..8 (two-kernel stage)
     double* rho;    // [np]
     double* ux;     // [np]
     double* uy;     // [np]
@@ -153,11 +156,6 @@ int launch_stage(const DevView& v, int prec, void* stream, const void* fin, cons
 // Most kernels launched by one stage (two-kernel strategy).
 constexpr int STAGE_KERNELS = 2;
 inline int stage_kernels(const DevView& v) { return v.strategy == STRATEGY_TILE ? 1 : 2; }
-// Dynamic shared memory of the fused stage kernel: f of the local cells and
-// the face values of the local faces, for real type of `rsize` bytes.
-inline size_t tile_smem_bytes_for(int ls, int fs, int rsize) {
-    return (size_t)rsize * ((size_t)FVLBM_Q * ls + (size_t)(FVLBM_Q - 1) * fs);
-}
 // One translation unit per state precision.
 int stage_fp64(const DevView& v, void* stream, const void* fin, const void* fbase, void* fout, double beta, int mode,
                void* const* ev);

@@ -87,10 +87,11 @@ size_t state_bytes(int prec) {
 }
 
 // Tile structure of the fused stage kernel.  Tiles are runs of consecutive
-// cells (internal order), at most `tile` long and cut shorter where the local
-// cells (tile, 1-ring = face neighbours outside the tile, 2-ring = their face
-// neighbours outside tile and 1-ring) or the tile's faces would exceed the
-// kernel's shared-memory capacity.  Every tile cell slot carries the local
+// cells (internal order), cut where tile and 1-ring (face neighbours outside
+// the tile) would exceed the CTA's `tile` threads, or where the local cells
+// (tile, 1-ring, 2-ring = face neighbours of the 1-ring outside tile and
+// 1-ring) or the tile's faces would exceed the kernel's shared-memory
+// capacity.  Every tile cell slot carries the local
 // index of its neighbour and the local index of its face; every 1-ring slot
 // the local index of its neighbour and, for faces shared with the tile, the
 // local face.
@@ -113,11 +114,13 @@ int64_t internal_nbr(const Mesh& M, int64_t i, int k) {
 }
 
 // Shared-memory capacity of the fused kernel for a tile size (TileDims).
-bool tile_dims(int tile, int maxf, int& ls, int& fs) {
-#define FVLBM_TD(T_)                                                                    \
-    case T_:                                                                            \
-        ls = maxf <= 4 ? TileDims<T_, 4>::LS : TileDims<T_, 8>::LS;                     \
-        fs = maxf <= 4 ? TileDims<T_, 4>::FS : TileDims<T_, 8>::FS;                     \
+bool tile_dims(int tile, int maxf, int rsize, int& ls, int& fs, size_t& bytes) {
+#define FVLBM_TD(T_)                                                                                         \
+    case T_:                                                                                                 \
+        ls = TileDims<T_, 4, 4>::LS;                                                                         \
+        fs = maxf <= 4 ? TileDims<T_, 4, 4>::FS : TileDims<T_, 8, 4>::FS;                                    \
+        bytes = maxf <= 4 ? (rsize == 4 ? TileDims<T_, 4, 4>::BYTES : TileDims<T_, 4, 8>::BYTES)             \
+                          : (rsize == 4 ? TileDims<T_, 8, 4>::BYTES : TileDims<T_, 8, 8>::BYTES);            \
         return true;
     switch (tile) {
         FVLBM_TD(128)
@@ -138,9 +141,11 @@ struct TileScratch {
 };
 
 // Local numbering of the tile [c0, c0 + len): tile cells, 1-ring, 2-ring, and
-// the local faces of the tile cells.  False when it exceeds ls / fs.
-bool try_tile(const Mesh& M, int maxf, int64_t c0, int len, int ls, int fs, TileScratch& W, int& n_local,
-              int& n_faces) {
+// the local faces of the tile cells.  False when it exceeds ls / fs, or when
+// tile and 1-ring together exceed the CTA's `threads` (the kernel gives every
+// thread at most one gradient to compute).
+bool try_tile(const Mesh& M, int maxf, int64_t c0, int len, int threads, int ls, int fs, TileScratch& W,
+              int& n_local, int& n_faces) {
     const int64_t g = ++W.gen;
     int nl = 0;
     for (int64_t i = c0; i < c0 + len; i++) {
@@ -167,8 +172,8 @@ bool try_tile(const Mesh& M, int maxf, int64_t c0, int len, int ls, int fs, Tile
                 W.r2.push_back(q);
             }
         }
-    if (nl > ls) return false;
     const int n1 = (int)W.r1.size();
+    if (nl > ls || len + n1 > threads) return false;
     W.t_nb.assign((size_t)len * maxf, -1);
     W.t_f.assign((size_t)len * maxf, -1);
     W.r_nb.assign((size_t)n1 * maxf, -1);
@@ -211,7 +216,8 @@ uint32_t pack_link(int nb, int f) {
 
 int make_tiles(const Mesh& M, int maxf, int tile, TilePlan& P) {
     int ls = 0, fs = 0;
-    if (!tile_dims(tile, maxf, ls, fs)) return fail(FVLBM_ERR_ARG, "unsupported tile size %d", tile);
+    size_t bytes = 0;
+    if (!tile_dims(tile, maxf, 4, ls, fs, bytes)) return fail(FVLBM_ERR_ARG, "unsupported tile size %d", tile);
     const int64_t n = M.n_cell;
     P = TilePlan{};
     P.tile = tile;
@@ -223,15 +229,17 @@ int make_tiles(const Mesh& M, int maxf, int tile, TilePlan& P) {
     W.stamp.assign(n, 0);
     W.loc.assign(n, 0);
     int64_t c0 = 0;
+    int guess = tile;   // neighbouring tiles have similar lengths: start one block above the last
     while (c0 < n) {
-        int len = (int)std::min<int64_t>(tile, n - c0);
+        int len = (int)std::min<int64_t>(guess, n - c0);
         int nl = 0, nf = 0;
-        while (!try_tile(M, maxf, c0, len, ls, fs, W, nl, nf)) {
+        while (!try_tile(M, maxf, c0, len, tile, ls, fs, W, nl, nf)) {
             if (len == 1)
                 return fail(FVLBM_ERR_UNSUPPORTED, "cell %lld: its halo exceeds the fused stage's capacity",
                             (long long)c0);
             len = len > BLK ? (len - 1) / BLK * BLK : len / 2;
         }
+        guess = std::min(tile, (len + BLK) / BLK * BLK);
         if (len < std::min<int64_t>(tile, n - c0)) P.short_tiles++;
         for (int li = 0; li < len; li++)
             for (int k = 0; k < maxf; k++) {
@@ -299,8 +307,12 @@ int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L, int 
     int tile = kernel;
     if (kernel == 0) {
         tile = 0;
-        for (int t = 1024; t >= 128 && !tile; t /= 2)
-            if ((M.n_cell + t - 1) / t >= sms) tile = t;
+        for (int t = 1024; t >= 128 && !tile; t /= 2) {
+            int ls = 0, fs = 0;
+            size_t smem = 0;
+            tile_dims(t, L.maxf, (int)R, ls, fs, smem);
+            if ((M.n_cell + t - 1) / t >= sms && smem <= SMEM_LIMIT) tile = t;
+        }
         if (prec == FVLBM_FP64) tile = 0;
     }
     L.strategy = tile == 0 || tile == 1 ? STRATEGY_TWO_KERNEL : STRATEGY_TILE;
@@ -308,8 +320,8 @@ int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L, int 
     while (L.block > 32 && (M.n_cell + L.block - 1) / L.block < 2 * sms) L.block /= 2;
     if (L.strategy == STRATEGY_TILE) {
         int ls = 0, fs = 0;
-        tile_dims(tile, L.maxf, ls, fs);
-        const size_t smem = tile_smem_bytes_for(ls, fs, (int)R);
+        size_t smem = 0;
+        tile_dims(tile, L.maxf, (int)R, ls, fs, smem);
         if (smem > SMEM_LIMIT)
             return fail(FVLBM_ERR_UNSUPPORTED, "fused stage with %d-cell tiles needs %zu B of shared memory (limit %zu)",
                         tile, smem, SMEM_LIMIT);

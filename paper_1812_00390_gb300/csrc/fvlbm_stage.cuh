@@ -52,8 +52,8 @@ __device__ __forceinline__ bool finite_val(T x) { return isfinite(x); }
 // Least-squares gradient (Eq. leastsquare) of f_1..f_8 of one cell from the
 // differences to its stencil values.  d: the cell's slot descriptors;
 // fnb(k, fj) fills fj[1..8] with the neighbour values across interior slot k.
-template <typename T, bool DEV, int MAXF, typename Nb>
-__device__ __forceinline__ void lsq_gradient(const uint2* d, const GeoRef<T, MAXF>& G, const BcParam* bcs, const T* f,
+template <typename T, bool DEV, int MAXF, typename Geo, typename Nb>
+__device__ __forceinline__ void lsq_gradient(const uint2* d, const Geo& G, const BcParam* bcs, const T* f,
                                              T rho, T ux, T uy, T* gx, T* gy, Nb fnb) {
 #pragma unroll
     for (int a = 0; a < FVLBM_Q - 1; a++) gx[a] = gy[a] = T(0);
@@ -90,8 +90,8 @@ __device__ __forceinline__ void lsq_gradient(const uint2* d, const GeoRef<T, MAX
 // table with direction stride `stride`: on interior faces the directions in
 // the slot's writer mask, on boundary faces every direction.  face(k) is the
 // slot's row in the table, or null to skip the slot.
-template <typename T, bool DEV, int MAXF, typename Row>
-__device__ __forceinline__ void write_faces(const uint2* d, const GeoRef<T, MAXF>& G, const BcParam* bcs, const T* f,
+template <typename T, bool DEV, int MAXF, typename Geo, typename Row>
+__device__ __forceinline__ void write_faces(const uint2* d, const Geo& G, const BcParam* bcs, const T* f,
                                             T rho, T ux, T uy, const T* gx, const T* gy, int64_t stride, Row face) {
 #pragma unroll
     for (int k = 0; k < MAXF; k++) {
@@ -121,20 +121,21 @@ __device__ __forceinline__ void write_faces(const uint2* d, const GeoRef<T, MAXF
 // (e_a . n dl / A) f_face (deviation mode: of f_face - f_a, the same in exact
 // arithmetic because the face vectors of a closed cell sum to zero, without
 // the rounding of the FP32 face vectors acting on the constant part of g).
-template <typename T, bool DEV, int MAXF, typename Row>
-__device__ __forceinline__ void flux_sum(const uint2* d, const typename Vec2<T>::type* n, const T* f, int64_t stride,
-                                         T* flux, Row face) {
+// face(k, fa) fills fa[0..7] with the values of directions 1..8 on slot k.
+template <typename T, bool DEV, int MAXF, typename Face>
+__device__ __forceinline__ void flux_sum(const uint2* d, const typename Vec2<T>::type* n, const T* f, T* flux,
+                                         Face face) {
 #pragma unroll
     for (int a = 0; a < FVLBM_Q; a++) flux[a] = T(0);
 #pragma unroll
     for (int k = 0; k < MAXF; k++) {
         if ((d[k].x & 0xFF) == SK_NONE) continue;
-        const T* fi = face(k);
+        T fa[FVLBM_Q - 1];
+        face(k, fa);
 #pragma unroll
         for (int a = 1; a < FVLBM_Q; a++) {
             const T en = T(EXA(a)) * n[k].x + T(EYA(a)) * n[k].y;
-            const T fa = fi[(a - 1) * stride];
-            flux[a] += en * (DEV ? fa - f[a] : fa);
+            flux[a] += en * (DEV ? fa[a - 1] - f[a] : fa[a - 1]);
         }
     }
 }
@@ -149,14 +150,36 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+template <typename V>
+__device__ __forceinline__ void cp_async_vec(V* dst, const V* src) {
+    static_assert(sizeof(V) == 8 || sizeof(V) == 16, "8- or 16-byte vector");
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(V) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
+}
+
+// Geometry of a cell whose least-squares and reconstruction vectors were
+// staged in shared memory (slot k: cg at k * STRIDE, rv at (MAXF + k) *
+// STRIDE); face vectors (boundary slots only) from global memory.
+template <typename T, int MAXF, int STRIDE> struct StagedGeo {
+    typedef typename Vec2<T>::type T2;
+    const T2* s;
+    GeoRef<T, MAXF> G;
+    __device__ __forceinline__ T2 cg(int k) const { return s[k * STRIDE]; }
+    __device__ __forceinline__ T2 rv(int k) const { return s[(MAXF + k) * STRIDE]; }
+    __device__ __forceinline__ T2 nv(int k) const { return G.nv(k); }
+};
 
 // Collision and time update of one cell (Eq. rhs, Sec. 2.3): rhs = -flux -
-// (f - f^eq) / tau, then out = base + beta dt rhs (multistage; fb the base
-// state, or null when it is f itself) or the AB2 combination.  Returns false
+// (f - f^eq) / tau, then out = base + beta dt rhs (multistage; the base state
+// is fb when use_fb, else f itself) or the AB2 combination.  Returns false
 // when an output is not finite.
 template <typename T, typename S, bool DEV>
 __device__ __forceinline__ bool update_cell(const DevView& v, const InstParam& P, int64_t i, const T* f, T rho, T ux,
-                                            T uy, const T* flux, const T* fb, S* fout, T beta, int mode) {
+                                            T uy, const T* flux, const T* fb, bool use_fb, S* fout, T beta,
+                                            int mode) {
     const T inv_tau = inst_inv_tau<T>(P);
     const T dt = inst_dt<T>(P);
     bool bad = false;
@@ -166,7 +189,7 @@ __device__ __forceinline__ bool update_cell(const DevView& v, const InstParam& P
     for (int a = 0; a < FVLBM_Q; a++) {
         const T rhs = -flux[a] - (f[a] - feqs<T, DEV>(a, rho, ux, uy)) * inv_tau;
         if (mode == MODE_RK) {
-            out[a] = (fb ? fb[a] : f[a]) + beta * dt * rhs;
+            out[a] = (use_fb ? fb[a] : f[a]) + beta * dt * rhs;
         } else if (mode == MODE_AB2_FIRST) {
             out[a] = f[a] + dt * rhs;
             rp[a * v.np + i] = rhs;
@@ -228,11 +251,15 @@ __global__ void __launch_bounds__(256) update_kernel(DevView v, const S* __restr
     moments<T, DEV>(f, rho, ux, uy);
     T flux[FVLBM_Q];
     const T* fv = (const T*)v.fv;
-    flux_sum<T, DEV, MAXF>(d, n, f, v.n_face, flux, [&](int k) { return fv + d[k].y; });
+    flux_sum<T, DEV, MAXF>(d, n, f, flux, [&](int k, T* fa) {
+        const T* p = fv + d[k].y;
+#pragma unroll
+        for (int a = 0; a < FVLBM_Q - 1; a++) fa[a] = p[a * v.n_face];
+    });
     T fb[FVLBM_Q];
     const bool rk_base = mode == MODE_RK && fbase != fin;
     if (rk_base) CellIO<S>::template load<T, DEV>(fbase, i, P, fb);
-    if (!update_cell<T, S, DEV>(v, P, i, f, rho, ux, uy, flux, rk_base ? fb : nullptr, fout, beta, mode))
+    if (!update_cell<T, S, DEV>(v, P, i, f, rho, ux, uy, flux, fb, rk_base, fout, beta, mode))
         *v.flag = 1;
 }
 
@@ -241,7 +268,7 @@ __global__ void __launch_bounds__(256) update_kernel(DevView v, const S* __restr
 // memory:
 //   phase 1  f of the tile, its 1-ring and its 2-ring (cp.async when the
 //            stored type is the arithmetic type)
-//   phase 2  per tile and 1-ring cell: the gradient (Eq. leastsquare), then
+//   phase 2  per tile and 1-ring cell (one per thread): the gradient (Eq. leastsquare), then
 //            its values on the tile's faces (Eq. lslrflux / Sec. 2.4.2): on
 //            interior faces the directions it writes (upwind side), on
 //            boundary faces (tile cells) every direction -- one writer per
@@ -255,12 +282,13 @@ template <typename T, typename S, int MAXF, bool DEV, int TILE>
 __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0 ? (sizeof(T) == 4 ? 1024 : 512) / TILE : 1)
     stage_tile_kernel(DevView v, const S* __restrict__ fin,
                                                           const S* fbase, S* fout, T beta, int mode) {
-    constexpr int LS = TileDims<TILE, MAXF>::LS;
-    constexpr int FS = TileDims<TILE, MAXF>::FS;
+    constexpr int LS = TileDims<TILE, MAXF, sizeof(T)>::LS;
+    constexpr int FS = TileDims<TILE, MAXF, sizeof(T)>::FS;
     typedef typename Vec2<T>::type T2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* fs = (T*)smem_raw;            // [9][LS]  f of the local cells
     T* fvs = fs + FVLBM_Q * LS;      // [8][FS]  face values of directions 1..8
+    T2* gst = (T2*)(fvs + (FVLBM_Q - 1) * FS);   // [2 MAXF][TILE] cg, rv of each thread's gradient cell
     const int64_t t = blockIdx.x;
     const int64_t c0 = v.tile_begin[t];
     const int nt = (int)(v.tile_begin[t + 1] - c0);
@@ -272,9 +300,11 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
     const bool mine = l < nt;          // this thread owns tile cell l
     const int64_t gi = c0 + l;
 
-    // phase 1
+    // phase 1 (thread l's first local cell is local cell l)
+    int64_t gl = c0;
     for (int x = l; x < nt + nh; x += TILE) {
         const int64_t gx = x < nt ? c0 + x : (int64_t)v.halo[h0 + (x - nt)];
+        if (x == l) gl = gx;
         if constexpr (sizeof(S) == sizeof(T)) {
             const S* p = fin + blk_index(gx, FVLBM_Q);
 #pragma unroll
@@ -286,61 +316,82 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
             for (int a = 0; a < FVLBM_Q; a++) fs[a * LS + x] = f[a];
         }
     }
-    // phase 2 geometry of the own cell, in flight during the wait
-    const GeoRef<T, MAXF> G(v.desc, v.geo, mine ? gi : c0);
-    uint2 d[MAXF];
-#pragma unroll
-    for (int k = 0; k < MAXF; k++) d[k] = mine ? G.desc(k) : make_uint2(SK_NONE, 0xFFFFFFFFu);
-    if constexpr (sizeof(S) == sizeof(T)) cp_async_wait_all();
-    __syncthreads();
-
-    // phase 2: the own tile cell, then 1-ring entries
-    if (mine) {
-        T f[FVLBM_Q];
-#pragma unroll
-        for (int a = 0; a < FVLBM_Q; a++) f[a] = fs[a * LS + l];
-        T rho, ux, uy;
-        moments<T, DEV>(f, rho, ux, uy);
-        T gx[FVLBM_Q - 1], gy[FVLBM_Q - 1];
-        lsq_gradient<T, DEV, MAXF>(d, G, v.bc, f, rho, ux, uy, gx, gy, [&](int k, T* fj) {
-            const T* p = fs + (d[k].y & 0xFFFF);
-#pragma unroll
-            for (int a = 1; a < FVLBM_Q; a++) fj[a] = p[a * LS];
-        });
-        write_faces<T, DEV, MAXF>(d, G, v.bc, f, rho, ux, uy, gx, gy, FS, [&](int k) { return fvs + (d[k].y >> 16); });
-    }
-    for (int e = l; e < n1; e += TILE) {
-        const int x = nt + e;
-        const int64_t gj = v.halo[h0 + e];
-        const GeoRef<T, MAXF> H(v.desc, v.geo, gj);
-        const uint32_t* rl = v.r1link + blk_index(q0 + e, MAXF);
-        uint2 dj[MAXF];
+    // Phase 2 gives local cell x (tile cell, or 1-ring entry x - nt) to thread
+    // x: with the planner's bound nt + n1 <= TILE every thread has at most one.
+    // Its descriptors and local links are in flight during the wait.
+    const int n2 = nt + n1;
+    auto links = [&](int x, int64_t g, uint2* d) {
+        const GeoRef<T, MAXF> H(v.desc, v.geo, g);
+        const uint32_t* rl = x < nt ? nullptr : v.r1link + blk_index(q0 + (x - nt), MAXF);
 #pragma unroll
         for (int k = 0; k < MAXF; k++) {
-            dj[k] = H.desc(k);
-            dj[k].y = rl[k * BLK];   // local links of the 1-ring entry
+            d[k] = H.desc(k);
+            if (x >= nt) d[k].y = rl[k * BLK];   // the 1-ring entry's local links
         }
+    };
+    uint2 d[MAXF];
+    if (l < n2) {
+        links(l, gl, d);
+        const GeoRef<T, MAXF> H(v.desc, v.geo, gl);
+#pragma unroll
+        for (int k = 0; k < MAXF; k++) {
+            cp_async_vec<T2>(gst + k * TILE + l, &H.g[(3 * k) * BLK]);
+            cp_async_vec<T2>(gst + (MAXF + k) * TILE + l, &H.g[(3 * k + 1) * BLK]);
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+
+    // phase 2
+    auto item = [&](int x, int64_t g, const uint2* dx) {
+        const StagedGeo<T, MAXF, TILE> H{gst + x, GeoRef<T, MAXF>(v.desc, v.geo, g)};
         T f[FVLBM_Q];
 #pragma unroll
         for (int a = 0; a < FVLBM_Q; a++) f[a] = fs[a * LS + x];
         T rho, ux, uy;
         moments<T, DEV>(f, rho, ux, uy);
         T gx[FVLBM_Q - 1], gy[FVLBM_Q - 1];
-        lsq_gradient<T, DEV, MAXF>(dj, H, v.bc, f, rho, ux, uy, gx, gy, [&](int k, T* fj) {
-            const T* p = fs + (dj[k].y & 0xFFFF);
+        lsq_gradient<T, DEV, MAXF>(dx, H, v.bc, f, rho, ux, uy, gx, gy, [&](int k, T* fj) {
+            const T* p = fs + (dx[k].y & 0xFFFF);
 #pragma unroll
             for (int a = 1; a < FVLBM_Q; a++) fj[a] = p[a * LS];
         });
-        // only faces shared with the tile; the 1-ring's boundary faces are not needed
-        write_faces<T, DEV, MAXF>(dj, H, v.bc, f, rho, ux, uy, gx, gy, FS, [&](int k) {
-            const uint32_t lf = dj[k].y >> 16;
-            return (lf == LINK_NONE || (dj[k].x & 0xFF) != SK_INTERIOR) ? (T*)nullptr : fvs + lf;
+        // tile cells write every face; 1-ring entries only the faces they share
+        // with the tile (their other links hold no local face)
+        write_faces<T, DEV, MAXF>(dx, H, v.bc, f, rho, ux, uy, gx, gy, FS, [&](int k) {
+            const uint32_t lf = dx[k].y >> 16;
+            return lf == LINK_NONE ? (T*)nullptr : fvs + lf;
+        });
+    };
+    if (l < n2) item(l, gl, d);
+    // never taken while the planner keeps nt + n1 <= TILE: the staged
+    // geometry has one row per thread
+    for (int x = l + TILE; x < n2; x += TILE) {
+        const int64_t g = (int64_t)v.halo[h0 + (x - nt)];
+        uint2 dx[MAXF];
+        links(x, g, dx);
+        const GeoRef<T, MAXF> H(v.desc, v.geo, g);
+        T f[FVLBM_Q];
+#pragma unroll
+        for (int a = 0; a < FVLBM_Q; a++) f[a] = fs[a * LS + x];
+        T rho, ux, uy;
+        moments<T, DEV>(f, rho, ux, uy);
+        T gx[FVLBM_Q - 1], gy[FVLBM_Q - 1];
+        lsq_gradient<T, DEV, MAXF>(dx, H, v.bc, f, rho, ux, uy, gx, gy, [&](int k, T* fj) {
+            const T* p = fs + (dx[k].y & 0xFFFF);
+#pragma unroll
+            for (int a = 1; a < FVLBM_Q; a++) fj[a] = p[a * LS];
+        });
+        write_faces<T, DEV, MAXF>(dx, H, v.bc, f, rho, ux, uy, gx, gy, FS, [&](int k) {
+            const uint32_t lf = dx[k].y >> 16;
+            return lf == LINK_NONE ? (T*)nullptr : fvs + lf;
         });
     }
     // phase 3 inputs, in flight during the wait
     T2 n[MAXF];
     T fb[FVLBM_Q];
     const bool rk_base = mode == MODE_RK && fbase != fin;
+    const GeoRef<T, MAXF> G(v.desc, v.geo, mine ? gi : c0);
     if (mine) {
 #pragma unroll
         for (int k = 0; k < MAXF; k++) n[k] = G.nv(k);
@@ -357,8 +408,12 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
     T rho, ux, uy;
     moments<T, DEV>(f, rho, ux, uy);
     T flux[FVLBM_Q];
-    flux_sum<T, DEV, MAXF>(d, n, f, FS, flux, [&](int k) { return fvs + (d[k].y >> 16); });
-    if (!update_cell<T, S, DEV>(v, P, gi, f, rho, ux, uy, flux, rk_base ? fb : nullptr, fout, beta, mode))
+    flux_sum<T, DEV, MAXF>(d, n, f, flux, [&](int k, T* fa) {
+        const T* p = fvs + (d[k].y >> 16);
+#pragma unroll
+        for (int a = 0; a < FVLBM_Q - 1; a++) fa[a] = p[a * FS];
+    });
+    if (!update_cell<T, S, DEV>(v, P, gi, f, rho, ux, uy, flux, fb, rk_base, fout, beta, mode))
         *v.flag = 1;
 }
 
@@ -375,7 +430,7 @@ template <typename T, typename S, int MAXF, bool DEV, int TILE>
 static int tile_launch(const DevView& v, cudaStream_t st, const void* fin, const void* fbase, void* fout,
                        double beta, int mode) {
     auto kern = stage_tile_kernel<T, S, MAXF, DEV, TILE>;
-    const size_t smem = tile_smem_bytes_for(TileDims<TILE, MAXF>::LS, TileDims<TILE, MAXF>::FS, (int)sizeof(T));
+    const size_t smem = TileDims<TILE, MAXF, sizeof(T)>::BYTES;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return fail(FVLBM_ERR_CUDA, "fused stage: %zu B shared memory: %s", smem, cudaGetErrorString(e));
@@ -384,16 +439,26 @@ static int tile_launch(const DevView& v, cudaStream_t st, const void* fin, const
     return FVLBM_OK;
 }
 
+// Tile sizes whose shared memory exceeds a CTA's are not instantiated (the
+// planner never selects them).
+constexpr size_t TILE_SMEM_LIMIT = 227 * 1024;
+
+template <typename T, typename S, int MAXF, bool DEV, int TILE>
+static int tile_launch_if_fits(const DevView& v, cudaStream_t st, const void* fin, const void* fbase, void* fout,
+                               double beta, int mode) {
+    if constexpr (TileDims<TILE, MAXF, sizeof(T)>::BYTES <= TILE_SMEM_LIMIT)
+        return tile_launch<T, S, MAXF, DEV, TILE>(v, st, fin, fbase, fout, beta, mode);
+    return fail(FVLBM_ERR_UNSUPPORTED, "tile size %d does not fit in shared memory", TILE);
+}
+
 template <typename T, typename S, int MAXF, bool DEV>
 static int tile_dispatch(const DevView& v, cudaStream_t st, const void* fin, const void* fbase, void* fout,
                          double beta, int mode) {
     switch (v.tile) {
-        case 128: return tile_launch<T, S, MAXF, DEV, 128>(v, st, fin, fbase, fout, beta, mode);
-        case 256: return tile_launch<T, S, MAXF, DEV, 256>(v, st, fin, fbase, fout, beta, mode);
-        case 512: return tile_launch<T, S, MAXF, DEV, 512>(v, st, fin, fbase, fout, beta, mode);
-        case 1024:   // FP64 tiles of 1024 cells do not fit in shared memory; the planner never makes them
-            if constexpr (sizeof(T) == 4) return tile_launch<T, S, MAXF, DEV, 1024>(v, st, fin, fbase, fout, beta, mode);
-            break;
+        case 128: return tile_launch_if_fits<T, S, MAXF, DEV, 128>(v, st, fin, fbase, fout, beta, mode);
+        case 256: return tile_launch_if_fits<T, S, MAXF, DEV, 256>(v, st, fin, fbase, fout, beta, mode);
+        case 512: return tile_launch_if_fits<T, S, MAXF, DEV, 512>(v, st, fin, fbase, fout, beta, mode);
+        case 1024: return tile_launch_if_fits<T, S, MAXF, DEV, 1024>(v, st, fin, fbase, fout, beta, mode);
     }
     return fail(FVLBM_ERR_ARG, "unsupported tile size %d", v.tile);
 }
