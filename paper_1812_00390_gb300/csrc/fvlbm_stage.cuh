@@ -15,35 +15,67 @@ template <> __device__ __forceinline__ double inst_inv_tau<double>(const InstPar
 template <> __device__ __forceinline__ float inst_inv_tau<float>(const InstParam& p) { return p.inv_tau_f; }
 
 // ------------------------------------------------------------------ physics
-// Stencil value minus the cell value for a boundary slot (Sec. 2.4.1):
+// Ghost state of a boundary slot (Sec. 2.4.1): the stencil value of direction
+// a minus the cell value is
 //   wall      f^eq(rho, u_w) - f^eq(rho, u)                        Eq. (wallbc)
-//   inlet     f^eq(rho*, u_inf) - f^eq(rho, u), rho* = rho_inf or rho
+//   inlet     f^eq(rho*, u_inf) - f^eq(rho, u), rho* = rho_inf (external) or rho
 //   outlet    0 (external) or f^eq(rho_inf, u) - f^eq(rho, u) (internal)
-//   symmetry  f^eq(rho, u*) - f, u* = u mirrored in the face line
-template <typename T, bool DEV>
-__device__ __forceinline__ T bc_delta(uint32_t kind, const BcParam& b, int a, T fa, T rho, T ux, T uy, T fe,
-                                      T nhx, T nhy) {
-    switch (kind) {
-        case SK_WALL: return feqs<T, DEV>(a, rho, T(b.uwx), T(b.uwy)) - fe;
-        case SK_INLET: return feqs<T, DEV>(a, b.external ? rarg<T, DEV>(b.rho_inf) : rho, T(b.uix), T(b.uiy)) - fe;
-        case SK_OUTLET: return b.external ? T(0) : feqs<T, DEV>(a, rarg<T, DEV>(b.rho_inf), ux, uy) - fe;
-        default: {  // symmetry
-            T un = ux * nhx + uy * nhy;
-            return feqs<T, DEV>(a, rho, ux - T(2) * un * nhx, uy - T(2) * un * nhy) - fa;
+//   symmetry  f^eq(rho, u*) - f_a, u* = u mirrored in the face line
+// i.e. f^eq(r, u_g) minus f^eq(rho, u) (or f_a for symmetry), with the ghost
+// density / velocity (r, u_g) found once per slot.
+template <typename T> struct Ghost {
+    T r, ux, uy;
+    bool zero;    // external outlet: no difference
+    bool sym;     // symmetry: subtract f_a
+    bool io;      // inlet / internal outlet: faces the cell flows out through are reconstructed
+};
+
+template <typename T, bool DEV, typename NormalFn>
+__device__ __forceinline__ Ghost<T> ghost_state(uint32_t kind, const BcParam& b, T rho, T ux, T uy, NormalFn normal) {
+    Ghost<T> g{rho, ux, uy, false, false, false};
+    if (kind == SK_WALL) {
+        g.ux = T(b.uwx);
+        g.uy = T(b.uwy);
+    } else if (kind == SK_INLET) {
+        if (b.external) g.r = rarg<T, DEV>(b.rho_inf);
+        g.ux = T(b.uix);
+        g.uy = T(b.uiy);
+        g.io = true;
+    } else if (kind == SK_OUTLET) {
+        if (b.external) {
+            g.zero = true;
+        } else {
+            g.r = rarg<T, DEV>(b.rho_inf);
+            g.io = true;
         }
+    } else {   // symmetry: the face's unit normal is needed only here
+        const typename Vec2<T>::type n = normal();
+        const T inv = T(1) / sqrt(n.x * n.x + n.y * n.y);
+        const T nhx = n.x * inv, nhy = n.y * inv;
+        const T un = ux * nhx + uy * nhy;
+        g.ux = ux - T(2) * un * nhx;
+        g.uy = uy - T(2) * un * nhy;
+        g.sym = true;
     }
+    return g;
 }
 
-// Face value of direction a on a boundary face (Sec. 2.4.2): external outlet
-// f_i; inlet / outlet faces the cell flows out through: the reconstruction
-// f_i + grad f_i . r; otherwise the ghost value (half way for symmetry).
+// Stencil value minus cell value of direction a (fe = f^eq_a(rho, u)).
 template <typename T, bool DEV>
-__device__ __forceinline__ T boundary_face(uint32_t kind, bool out, const BcParam& b, int a, T fa, T rho, T ux, T uy,
-                                           T gxa, T gya, T rx, T ry, T nhx, T nhy) {
-    if (kind == SK_OUTLET && b.external) return fa;
-    if ((kind == SK_INLET || kind == SK_OUTLET) && out) return fa + gxa * rx + gya * ry;
-    const T d = bc_delta<T, DEV>(kind, b, a, fa, rho, ux, uy, feqs<T, DEV>(a, rho, ux, uy), nhx, nhy);
-    return kind == SK_SYMMETRY ? fa + T(0.5) * d : fa + d;
+__device__ __forceinline__ T ghost_delta(const Ghost<T>& g, int a, T fa, T fe) {
+    if (g.zero) return T(0);
+    return feqs<T, DEV>(a, g.r, g.ux, g.uy) - (g.sym ? fa : fe);
+}
+
+// Face value of direction a on a boundary face (Sec. 2.4.2): inlet / internal
+// outlet faces the cell flows out through: the reconstruction
+// f_i + grad f_i . r; otherwise the ghost value (half way for symmetry; the
+// cell value at an external outlet).
+template <typename T, bool DEV>
+__device__ __forceinline__ T boundary_face(const Ghost<T>& g, bool out, int a, T fa, T fe, T gxa, T gya, T rx, T ry) {
+    if (g.io && out) return fa + gxa * rx + gya * ry;
+    const T d = ghost_delta<T, DEV>(g, a, fa, fe);
+    return g.sym ? fa + T(0.5) * d : fa + d;
 }
 
 template <typename T>
@@ -72,13 +104,10 @@ __device__ __forceinline__ void lsq_gradient(const uint2* d, const Geo& G, const
                 gy[a - 1] += c.y * dd;
             }
         } else {
-            const BcParam& b = bcs[d[k].x >> 16];
-            const typename Vec2<T>::type n = G.nv(k);
-            const T inv = T(1) / sqrt(n.x * n.x + n.y * n.y);
+            const Ghost<T> g = ghost_state<T, DEV>(kind, bcs[d[k].x >> 16], rho, ux, uy, [&] { return G.nv(k); });
 #pragma unroll
             for (int a = 1; a < FVLBM_Q; a++) {
-                const T dd = bc_delta<T, DEV>(kind, b, a, f[a], rho, ux, uy, feqs<T, DEV>(a, rho, ux, uy), n.x * inv,
-                                              n.y * inv);
+                const T dd = ghost_delta<T, DEV>(g, a, f[a], feqs<T, DEV>(a, rho, ux, uy));
                 gx[a - 1] += c.x * dd;
                 gy[a - 1] += c.y * dd;
             }
@@ -106,13 +135,12 @@ __device__ __forceinline__ void write_faces(const uint2* d, const Geo& G, const 
             for (int a = 1; a < FVLBM_Q; a++)
                 if (mask & (1u << (a - 1))) fo[(a - 1) * stride] = f[a] + gx[a - 1] * r.x + gy[a - 1] * r.y;
         } else {
-            const BcParam& b = bcs[d[k].x >> 16];
-            const typename Vec2<T>::type n = G.nv(k);
-            const T inv = T(1) / sqrt(n.x * n.x + n.y * n.y);
+            const Ghost<T> g = ghost_state<T, DEV>(kind, bcs[d[k].x >> 16], rho, ux, uy, [&] { return G.nv(k); });
 #pragma unroll
             for (int a = 1; a < FVLBM_Q; a++)
-                fo[(a - 1) * stride] = boundary_face<T, DEV>(kind, (mask >> (a - 1)) & 1u, b, a, f[a], rho, ux, uy,
-                                                             gx[a - 1], gy[a - 1], r.x, r.y, n.x * inv, n.y * inv);
+                fo[(a - 1) * stride] = boundary_face<T, DEV>(g, (mask >> (a - 1)) & 1u, a, f[a],
+                                                             feqs<T, DEV>(a, rho, ux, uy), gx[a - 1], gy[a - 1], r.x,
+                                                             r.y);
         }
     }
 }
