@@ -85,7 +85,7 @@ def build_solver(fv, variants, inst, precision, scheme="rk2", handles=None, kern
     return fv.Solver(mesh, params), handles
 
 
-def tune_kernel(fv, handles, inst, precision, scheme="rk2", n_sample=24, steps=20):
+def tune_kernel(fv, handles, inst, precision, scheme="rk2", n_sample=64, steps=20):
     """Stage-kernel variant chosen by the library's autotuner on the first
     n_sample instances of the batch (all three kinds)."""
     sub = inst[:n_sample]
@@ -223,8 +223,12 @@ def measured_peaks():
 
 
 def kernel_source_sha() -> str:
-    src = os.path.join(ROOT, "paper_1812_00390_gb300", "csrc", "fvlbm_stage.cuh")
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    """Hash of the sources that decide what the stage kernels do and read: the
+    kernels, the device layout and the host-side tile planner."""
+    h = hashlib.sha256()
+    for f in ("fvlbm_stage.cuh", "fvlbm_device.cuh", "fvlbm_internal.h", "fvlbm_solver.cpp"):
+        h.update(open(os.path.join(ROOT, "paper_1812_00390_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic(workload: str):

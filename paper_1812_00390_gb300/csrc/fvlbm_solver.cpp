@@ -290,10 +290,11 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 // kernel: 1 two-kernel, 128/256/512/1024 fused with that tile size, 0
 // automatic: FP64 takes the two-kernel stage (it spends fewer FP64 operations);
-// the other precisions take the largest tile that still gives every SM a tile
-// of its own, or the two-kernel stage when even 128-cell tiles would leave SMs
-// idle.  The two-kernel stage shrinks its blocks (down to 32 threads) for the
-// same reason.
+// the other precisions take 512-thread tiles (the fastest measured on large
+// batches) when there are enough cells for every SM, else the largest smaller
+// tile that still gives every SM a tile of its own, or the two-kernel stage
+// when even 128-thread tiles would leave SMs idle.  The two-kernel stage
+// shrinks its blocks (down to 32 threads) for the same reason.
 int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L, int sms) {
     L = Layout{};
     L.np = round_up(M.n_cell, PLANE_ALIGN);
@@ -307,7 +308,7 @@ int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L, int 
     int tile = kernel;
     if (kernel == 0) {
         tile = 0;
-        for (int t = 1024; t >= 128 && !tile; t /= 2) {
+        for (int t = 512; t >= 128 && !tile; t /= 2) {
             int ls = 0, fs = 0;
             size_t smem = 0;
             tile_dims(t, L.maxf, (int)R, ls, fs, smem);
