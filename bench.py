@@ -138,6 +138,38 @@ def config_runs(fv, torch, dev, steps: int = 30):
     return out
 
 
+def roofline_synthetic(fv, torch, peak_gbs, steps: int = 20):
+    """The interior-only roofline case: a fully periodic jittered-triangle domain
+    of 2048 x 1024 x 2 = 4,194,304 cells (no boundary faces; state and geometry
+    far larger than L2), uniform flow (the kernels do the same work for any
+    state), RK2, in FP64, FP32 and FP16 split storage, each with the automatic
+    stage kernel.  Per precision: MCUPS and the stage kernels' algorithmic HBM
+    rate (state bytes only: 5 x the stored bytes per cell and RK2 step)."""
+    from paper_1812_00390_gb300 import meshgen as mg
+    m = mg.periodic_tri(2048, 1024, lx=2048.0, ly=1024.0, seed=2048)
+    h = fv.Mesh(m)
+    out = {"cells": m.n_cell, "mesh": "periodic jittered triangles 2048 x 1024 x 2", "scheme": "rk2"}
+    for prec, sb in (("fp32", 36), ("fp16", 24), ("fp64", 72)):   # stored bytes per cell
+        s = fv.Solver(h, fv.make_params(0.1, scheme="rk2", precision=prec, u0=(0.02, 0.01)))
+        s.step(3)
+        s.sync()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s.stream)
+        s.step(steps)
+        e.record(s.stream)
+        s.sync()
+        ms = a.elapsed_time(e) / steps
+        kern, _ = s.profile(3)
+        stage_ms = float(sum(kern))
+        alg = 5 * sb / 2 * m.n_cell               # bytes per stage (mean of the two RK2 stages)
+        out[prec] = {"mcups": m.n_cell / (ms / 1e3) / 1e6, "ms_per_step": ms, "stage_ms": stage_ms,
+                     "stage_kernel": "two-kernel" if len(kern) == 2 else "fused 512",
+                     "algorithmic_gbs": alg / (stage_ms / 1e3) / 1e9,
+                     "frac_of_hbm_peak": alg / (stage_ms / 1e3) / 1e9 / peak_gbs}
+        s.close()
+    return out
+
+
 # ----------------------------------------------------------------------------- ranks
 def reduce_max(x: float, dist, device=None) -> float:
     """Largest value over all ranks (the slowest rank's time); x itself at N = 1."""
@@ -209,6 +241,9 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- roofline inputs
+GEOMETRY_BYTES_FP32 = 4 * (8 + 3 * 2 * 4)   # per cell and stage, 4 face slots
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -436,6 +471,15 @@ def run_ours(args):
                        else "one RK2 stage = face_values_kernel + update_kernel"),
             "kernel_ms": {n: float(t) for n, t in zip(names, kern_ms)},
             "algorithmic_bytes_per_launch": alg_per_cell_stage * n_cells,
+            # the same with the per-slot geometry the stage reads (8-byte descriptor and three
+            # FP32 2-vectors per slot, 4 slots): 90 + 128 B per cell and stage
+            "with_geometry": {"bytes_per_launch": (alg_per_cell_stage + GEOMETRY_BYTES_FP32) * n_cells,
+                              "achieved": (alg_per_cell_stage + GEOMETRY_BYTES_FP32) * n_cells
+                              / (stage_ms / 1e3) / 1e9,
+                              "frac": (alg_per_cell_stage + GEOMETRY_BYTES_FP32) * n_cells
+                              / (stage_ms / 1e3) / 1e9 / peak},
+            # ncu's DRAM bytes per launch over the live launch time
+            "dram_frac": (traffic_pc * n_cells / (stage_ms / 1e3) / 1e9 / peak if traffic_pc else None),
             "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
             else f"{peak_src} {HBM_FALLBACK_GBS:.0f} GB/s"}
 
@@ -458,6 +502,7 @@ def run_ours(args):
         e2e_val = n_cells * world * e2e_inner * args.e2e_steps / e2e_s / 1e6
 
     configs = config_runs(fv, torch, dev) if (args.configs and rank == 0) else None
+    roof_syn = roofline_synthetic(fv, torch, peak) if (args.configs and rank == 0) else None
 
     # serving stream (config 5): Poisson arrivals of tandem / single cylinder
     # solves on the continuous-batching server, p50 / p99 time to completion
@@ -503,6 +548,7 @@ def run_ours(args):
                     if e2e_val is not None else None),
             "serving": serving,
             "single_configs": configs,
+            "roofline_synthetic": roof_syn,
             "gpu_launches": launches,
             "clocks": clocks,
         }
