@@ -248,6 +248,25 @@ int fvlbm_mass_noalloc(fvlbm_solver* s, double* mass);
 int fvlbm_get_f(fvlbm_solver* s, double* f);
 int fvlbm_set_f(fvlbm_solver* s, const double* f);
 
+/*
+ * How fvlbm_get_f, fvlbm_set_f and fvlbm_macros move data between the
+ * caller's host buffers and the device.
+ *   FVLBM_HOST_AUTO (the default): when the device reports coherent access to
+ *     pageable host memory (cudaDevAttrPageableMemoryAccess; GB300 reaches its
+ *     Grace host's memory over NVLink-C2C), the kernels read and write the
+ *     caller's buffer directly, in the caller's cell order: no host-side
+ *     reordering, no staging copy.  Otherwise as FVLBM_HOST_STAGED.
+ *   FVLBM_HOST_STAGED: the library reorders on the host and copies through a
+ *     staging buffer of its own.
+ * The buffers passed to those calls must be ordinary host memory (malloc,
+ * numpy, pinned) or device memory; the calls synchronise before returning, so
+ * the caller may reuse them at once.  The results are bitwise the same in both
+ * modes.  direct: host, optional, written: 1 when the kernels access the
+ * caller's buffers directly.  Errors: FVLBM_ERR_ARG.
+ */
+typedef enum fvlbm_host_mode { FVLBM_HOST_AUTO = 0, FVLBM_HOST_STAGED = 1 } fvlbm_host_mode;
+int fvlbm_host_transfer(fvlbm_solver* s, int32_t mode, int32_t* direct);
+
 /* Wait for the solver's stream; reports FVLBM_ERR_DIVERGED if flagged. */
 int fvlbm_sync(fvlbm_solver* s);
 

@@ -115,6 +115,7 @@ struct DevView {
     const int32_t* nbr;
     const double* area;    // [np]
     const int32_t* grp;    // [np] instance of each cell
+    const int32_t* iperm;  // [n_cell] internal index of each cell in the caller's order
     const InstParam* inst; // [n_inst]
     const BcParam* bc;     // [n_bc]
     // state
@@ -169,6 +170,12 @@ int launch_macros(const DevView& v, int prec, void* stream);
 int launch_reduce(const DevView& v, void* stream, int what);
 int launch_get_f(const DevView& v, int prec, void* stream);
 int launch_set_f(const DevView& v, int prec, void* stream);
+// The same, and the macros, on a caller's buffer in the caller's cell order
+// that the device accesses directly (host memory reachable by the GPU, or
+// device memory).
+int launch_get_f_direct(const DevView& v, int prec, void* stream, double* f);
+int launch_set_f_direct(const DevView& v, int prec, void* stream, const double* f);
+int launch_macros_direct(const DevView& v, int prec, void* stream, double* rho, double* u);
 
 // Solver internals for entry points defined outside the solver's own file.
 struct SolverRef {

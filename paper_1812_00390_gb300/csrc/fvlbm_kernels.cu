@@ -76,6 +76,47 @@ __global__ void set_f_kernel(DevView v) {
     CellIO<S>::template store<T, DEV>(v.fa, i, v.inst[v.grp[i]], f);
 }
 
+// Direct access to a caller's buffer in caller order [n_cell][9] (get / set)
+// or [n_cell] and [n_cell][2] (macros): one thread per caller cell c, so that
+// the caller's buffer is read and written contiguously.
+template <typename T, typename S, bool DEV>
+__global__ void get_f_direct_kernel(DevView v, double* __restrict__ out) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= v.n_cell) return;
+    const int64_t i = v.iperm[c];
+    T f[FVLBM_Q];
+    CellIO<S>::template load<T, DEV>(v.fa, i, v.inst[v.grp[i]], f);
+    for (int a = 0; a < FVLBM_Q; a++) out[c * FVLBM_Q + a] = DEV ? (double)f[a] + wgt<double>(a) : (double)f[a];
+}
+
+template <typename T, typename S, bool DEV>
+__global__ void set_f_direct_kernel(DevView v, const double* __restrict__ in) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= v.n_cell) return;
+    const int64_t i = v.iperm[c];
+    T f[FVLBM_Q];
+    for (int a = 0; a < FVLBM_Q; a++) {
+        const double x = in[c * FVLBM_Q + a];
+        f[a] = (T)(DEV ? x - wgt<double>(a) : x);
+    }
+    CellIO<S>::template store<T, DEV>(v.fa, i, v.inst[v.grp[i]], f);
+}
+
+template <typename T, typename S, bool DEV>
+__global__ void macros_direct_kernel(DevView v, double* __restrict__ rho_out, double* __restrict__ u_out) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= v.n_cell) return;
+    const int64_t i = v.iperm[c];
+    double r, mx, my;
+    CellIO<S>::moments64(v.fa, i, v.inst[v.grp[i]], r, mx, my);
+    const double rho = DEV ? 1.0 + r : r;
+    if (rho_out) rho_out[c] = rho;
+    if (u_out) {
+        u_out[2 * c] = mx / rho;
+        u_out[2 * c + 1] = my / rho;
+    }
+}
+
 // Deterministic FP64 reductions: one block per chunk of one instance, fixed
 // tree order; then one thread per instance sums its chunks in order.
 constexpr int RED_THREADS = 256;
@@ -232,3 +273,23 @@ extern "C" int fvlbm_fma_peak(int32_t device, int32_t fp64, double* tflops) {
     if (prev >= 0) cudaSetDevice(prev);
     return rc;
 }
+
+namespace fvlbm {
+int launch_get_f_direct(const DevView& v, int prec, void* stream, double* f) {
+    cudaStream_t st = (cudaStream_t)stream;
+    DISPATCH_PREC(prec, get_f_direct_kernel<T, S, DEV><<<grid_of(v.n_cell, 256), 256, 0, st>>>(v, f);
+                  return check_launch("get_f kernel"));
+}
+
+int launch_set_f_direct(const DevView& v, int prec, void* stream, const double* f) {
+    cudaStream_t st = (cudaStream_t)stream;
+    DISPATCH_PREC(prec, set_f_direct_kernel<T, S, DEV><<<grid_of(v.n_cell, 256), 256, 0, st>>>(v, f);
+                  return check_launch("set_f kernel"));
+}
+
+int launch_macros_direct(const DevView& v, int prec, void* stream, double* rho, double* u) {
+    cudaStream_t st = (cudaStream_t)stream;
+    DISPATCH_PREC(prec, macros_direct_kernel<T, S, DEV><<<grid_of(v.n_cell, 256), 256, 0, st>>>(v, rho, u);
+                  return check_launch("macros kernel"));
+}
+}  // namespace fvlbm

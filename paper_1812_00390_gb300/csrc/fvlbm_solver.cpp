@@ -36,6 +36,9 @@ struct fvlbm_solver {
     DevView v{};
     std::vector<InstParam> inst;
     bool ab2_started = false;
+    // the device reads / writes the caller's host buffers directly (see fvlbm_host_transfer)
+    bool host_can_direct = false;
+    bool host_direct = false;
     std::vector<double> h_conv, h_rho, h_ux, h_uy;
     // single-stage schemes on the fused stage alternate the state between
     // buf[0] and buf[1] (a tile must not overwrite cells other tiles still
@@ -270,7 +273,7 @@ struct Layout {
     TilePlan tp;
     size_t off_desc, off_geo, off_nbr, off_area, off_grp, off_inst, off_bc, off_fa, off_fb, off_rprev, off_fv,
         off_rho, off_ux, off_uy, off_uold, off_part, off_red, off_conv, off_chunk, off_flag, off_tbegin, off_hptr,
-        off_halo, off_r1ptr, off_r1link, total;
+        off_halo, off_r1ptr, off_r1link, off_iperm, total;
 };
 
 constexpr size_t SMEM_LIMIT = 227 * 1024;
@@ -344,6 +347,7 @@ int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L, int 
     L.off_nbr = take(two ? 4 * slots : 0);
     L.off_area = take(8 * plane);
     L.off_grp = take(4 * plane);
+    L.off_iperm = take(4 * plane);
     L.off_inst = take(sizeof(InstParam) * M.n_inst);
     L.off_bc = take(sizeof(BcParam) * std::max<size_t>(1, M.bcs.size()));
     L.off_tbegin = take(tiled ? 8 * (size_t)(L.tp.n_tiles + 1) : 0);
@@ -369,6 +373,7 @@ int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L, int 
 }
 
 int check_params(const Mesh& M, const fvlbm_params* params, int32_t n_params) {
+    if (M.n_cell >= ((int64_t)1 << 31)) return fail(FVLBM_ERR_ARG, "more than 2^31 - 1 cells");
     if (!params || !(n_params == 1 || n_params == M.n_inst))
         return fail(FVLBM_ERR_ARG, "params: need 1 or %d entries, got %d", M.n_inst, n_params);
     for (int32_t k = 0; k < n_params; k++) {
@@ -428,6 +433,8 @@ void pack_geometry(const Mesh& M, const Layout& L, std::vector<unsigned char>& h
     T* geo = (T*)(H + L.off_geo);                   // pairs of T
     double* area = (double*)(H + L.off_area);
     int32_t* grp = (int32_t*)(H + L.off_grp);
+    int32_t* iperm = (int32_t*)(H + L.off_iperm);
+    for (int64_t c = 0; c < n; c++) iperm[c] = (int32_t)M.iperm[c];
     int32_t* nbr = two ? (int32_t*)(H + L.off_nbr) : nullptr;
     for (size_t x = 0; x < (size_t)maxf * L.np; x++) {
         desc[2 * x] = SK_NONE;
@@ -517,6 +524,13 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
     s->n_inst = M.n_inst;
     s->perm = M.perm;
     s->inst_begin = M.inst_begin;
+    int pageable = 0;
+    if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, p0.device) != cudaSuccess) {
+        cudaGetLastError();
+        pageable = 0;
+    }
+    s->host_can_direct = pageable == 1;
+    s->host_direct = s->host_can_direct;
 
     // per-instance constants and the time step of Eqs. (CFL), (timetau)
     s->inst.resize(M.n_inst);
@@ -637,6 +651,7 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
     v.nbr = (const int32_t*)(base + L.off_nbr);
     v.area = (const double*)(base + L.off_area);
     v.grp = (const int32_t*)(base + L.off_grp);
+    v.iperm = (const int32_t*)(base + L.off_iperm);
     v.inst = (const InstParam*)(base + L.off_inst);
     v.bc = (const BcParam*)(base + L.off_bc);
     v.fa = base + L.off_fa;
@@ -913,6 +928,10 @@ extern "C" int fvlbm_macros(fvlbm_solver* s, double* rho, double* u) {
     clear_error();
     if (!s) return fail(FVLBM_ERR_ARG, "fvlbm_macros: null solver");
     DeviceGuard dg(s->device);
+    if (s->host_direct) {
+        int rc = launch_macros_direct(s->v, s->prec, s->stream, rho, u);
+        return rc ? rc : sync_and_check(s);
+    }
     int rc = launch_macros(s->v, s->prec, s->stream);
     if (rc) return rc;
     const size_t bytes = 8 * (size_t)s->n_cell;
@@ -971,6 +990,10 @@ extern "C" int fvlbm_get_f(fvlbm_solver* s, double* f) {
     clear_error();
     if (!s || !f) return fail(FVLBM_ERR_ARG, "fvlbm_get_f: null argument");
     DeviceGuard dg(s->device);
+    if (s->host_direct) {
+        int rc = launch_get_f_direct(s->v, s->prec, s->stream, f);
+        return rc ? rc : sync_and_check(s);
+    }
     int rc = launch_get_f(s->v, s->prec, s->stream);
     if (rc) return rc;
     CK(cudaMemcpyAsync(s->h_conv.data(), s->v.conv, 8 * (size_t)s->v.np * FVLBM_Q, cudaMemcpyDeviceToHost, s->stream),
@@ -989,17 +1012,32 @@ extern "C" int fvlbm_set_f(fvlbm_solver* s, const double* f) {
     if (!s || !f) return fail(FVLBM_ERR_ARG, "fvlbm_set_f: null argument");
     DeviceGuard dg(s->device);
     CK(cudaStreamSynchronize(s->stream), "synchronise");
-    for (int64_t i = 0; i < s->n_cell; i++) {
-        const int64_t c = s->perm[i];
-        for (int a = 0; a < FVLBM_Q; a++) s->h_conv[(size_t)a * s->v.np + i] = f[c * FVLBM_Q + a];
+    int rc;
+    if (s->host_direct) {
+        rc = launch_set_f_direct(s->v, s->prec, s->stream, f);
+    } else {
+        for (int64_t i = 0; i < s->n_cell; i++) {
+            const int64_t c = s->perm[i];
+            for (int a = 0; a < FVLBM_Q; a++) s->h_conv[(size_t)a * s->v.np + i] = f[c * FVLBM_Q + a];
+        }
+        CK(cudaMemcpyAsync(s->v.conv, s->h_conv.data(), 8 * (size_t)s->v.np * FVLBM_Q, cudaMemcpyHostToDevice,
+                           s->stream),
+           "write f");
+        rc = launch_set_f(s->v, s->prec, s->stream);
     }
-    CK(cudaMemcpyAsync(s->v.conv, s->h_conv.data(), 8 * (size_t)s->v.np * FVLBM_Q, cudaMemcpyHostToDevice, s->stream),
-       "write f");
-    int rc = launch_set_f(s->v, s->prec, s->stream);
     if (rc) return rc;
     s->ab2_started = false;
     if (s->scheme == FVLBM_AB2) s->direct_steps = 0;   // the next step is an Euler start, launched directly
     CK(cudaStreamSynchronize(s->stream), "synchronise");
+    return FVLBM_OK;
+}
+
+extern "C" int fvlbm_host_transfer(fvlbm_solver* s, int32_t mode, int32_t* direct) {
+    clear_error();
+    if (!s || (mode != FVLBM_HOST_AUTO && mode != FVLBM_HOST_STAGED))
+        return fail(FVLBM_ERR_ARG, "fvlbm_host_transfer: bad arguments");
+    s->host_direct = mode == FVLBM_HOST_AUTO && s->host_can_direct;
+    if (direct) *direct = s->host_direct ? 1 : 0;
     return FVLBM_OK;
 }
 

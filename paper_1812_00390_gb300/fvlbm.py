@@ -72,7 +72,7 @@ class ServerStatsT(C.Structure):
 #: every symbol include/fvlbm.h declares
 EXPORTS = ["fvlbm_mesh_create", "fvlbm_mesh_concat", "fvlbm_mesh_destroy", "fvlbm_mesh_info",
            "fvlbm_suggest_dt", "fvlbm_workspace_bytes", "fvlbm_init", "fvlbm_step", "fvlbm_macros",
-           "fvlbm_residual", "fvlbm_mass", "fvlbm_mass_noalloc", "fvlbm_get_f", "fvlbm_set_f", "fvlbm_sync",
+           "fvlbm_residual", "fvlbm_mass", "fvlbm_mass_noalloc", "fvlbm_get_f", "fvlbm_set_f", "fvlbm_host_transfer", "fvlbm_sync",
            "fvlbm_get_dt", "fvlbm_profile", "fvlbm_autotune", "fvlbm_fma_peak", "fvlbm_launches_per_step", "fvlbm_solver_destroy",
            "fvlbm_server_create", "fvlbm_server_submit", "fvlbm_server_poll", "fvlbm_server_request",
            "fvlbm_server_stats", "fvlbm_server_destroy", "fvlbm_last_error"]
@@ -110,6 +110,7 @@ def _load():
         "fvlbm_launches_per_step": [P, i64p],
         "fvlbm_autotune": [P, C.POINTER(ParamsT), C.c_int32, P, C.c_int32, i32p, dp],
         "fvlbm_fma_peak": [C.c_int32, C.c_int32, dp],
+        "fvlbm_host_transfer": [P, C.c_int32, i32p],
         "fvlbm_solver_destroy": [P],
         "fvlbm_server_create": [C.POINTER(ServerConfigT), PP],
         "fvlbm_server_submit": [P, P, C.POINTER(ParamsT), C.c_int32, i64p],
@@ -294,6 +295,14 @@ class Solver:
     def set_f(self, f):
         f = np.ascontiguousarray(f, np.float64).reshape(self.n_cell, 9)
         _check(lib.fvlbm_set_f(self._h, _d(f)))
+
+    def host_transfer(self, mode: str = "auto") -> bool:
+        """How get_f / set_f / macros reach host buffers: "auto" (direct device
+        access when the GPU can reach pageable host memory) or "staged".
+        Returns True when the direct path is in use."""
+        d = C.c_int32()
+        _check(lib.fvlbm_host_transfer(self._h, {"auto": 0, "staged": 1}[mode], C.byref(d)))
+        return bool(d.value)
 
     def dt(self, instance: int = 0) -> float:
         d = C.c_double()
