@@ -259,10 +259,17 @@ def measured_peaks():
 
 def kernel_source_sha() -> str:
     """Hash of the sources that decide what the stage kernels do and read: the
-    kernels, the device layout and the host-side tile planner."""
+    kernels and the device storage (whole files), the shared-memory capacities
+    and the host-side tile planner (their sections of the other files)."""
+    csrc = os.path.join(ROOT, "paper_1812_00390_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("fvlbm_stage.cuh", "fvlbm_device.cuh", "fvlbm_internal.h", "fvlbm_solver.cpp"):
-        h.update(open(os.path.join(ROOT, "paper_1812_00390_gb300", "csrc", f), "rb").read())
+    for f in ("fvlbm_stage.cuh", "fvlbm_device.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    for f, begin, end in (("fvlbm_internal.h", "struct TileDims", "};"),
+                          ("fvlbm_solver.cpp", "struct TilePlan {", "// Offsets of every array")):
+        txt = open(os.path.join(csrc, f)).read()
+        a = txt.index(begin)
+        h.update(txt[a:txt.index(end, a)].encode())
     return h.hexdigest()[:16]
 
 
