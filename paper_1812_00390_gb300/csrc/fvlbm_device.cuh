@@ -65,10 +65,10 @@ __host__ __device__ __forceinline__ int64_t blk_index(int64_t i, int ncomp) {
 // mode, the stored quantity is g = f - w).
 //  double / float   9 components per cell: g_a (f_a in FP64 mode).
 //  __half / bf16    split format: 3 FP32 components rho - 1, rho u_x, rho u_y,
-//                   then six 16-bit components: the non-equilibrium parts
+//                   then the six 16-bit non-equilibrium parts
 //                   n_a = g_a - g^eq_a(rho, u) of directions a = 3..8, times
-//                   a power-of-two scale per (instance, direction).  A block
-//                   is 32 x 3 floats followed by 32 x 6 16-bit values.
+//                   a power-of-two scale per (instance, direction), packed in
+//                   pairs into three 32-bit components.
 //                   n_0, n_1, n_2 follow from sum_a n_a = 0 and
 //                   sum_a e_a n_a = 0 (the non-equilibrium part carries no mass
 //                   or momentum), so rho and u never round through 16 bits;
@@ -104,33 +104,42 @@ template <typename S> struct PlainIO {
 template <> struct CellIO<double> : PlainIO<double> {};
 template <> struct CellIO<float> : PlainIO<float> {};
 
-template <typename H> __device__ __forceinline__ float h2f(H x);
-template <> __device__ __forceinline__ float h2f<__half>(__half x) { return __half2float(x); }
-template <> __device__ __forceinline__ float h2f<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
-template <typename H> __device__ __forceinline__ H f2h(float x);
-template <> __device__ __forceinline__ __half f2h<__half>(float x) { return __float2half_rn(x); }
-template <> __device__ __forceinline__ __nv_bfloat16 f2h<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <typename H> __device__ __forceinline__ uint32_t h_bits(float x);
+template <> __device__ __forceinline__ uint32_t h_bits<__half>(float x) { return __half_as_ushort(__float2half_rn(x)); }
+template <> __device__ __forceinline__ uint32_t h_bits<__nv_bfloat16>(float x) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+template <typename H> __device__ __forceinline__ float h_value(uint32_t bits);
+template <> __device__ __forceinline__ float h_value<__half>(uint32_t bits) {
+    return __half2float(__ushort_as_half((unsigned short)bits));
+}
+template <> __device__ __forceinline__ float h_value<__nv_bfloat16>(uint32_t bits) {
+    return __bfloat162float(__ushort_as_bfloat16((unsigned short)bits));
+}
 
+// Split format: a block of 32 cells holds 3 x 32 floats (rho - 1, rho u_x,
+// rho u_y), then 3 x 32 words, word q of a cell packing n_{3+2q} (low 16
+// bits) and n_{4+2q} (high 16 bits).
 template <typename H> struct SplitIO {
-    static constexpr int64_t BLOCK_BYTES = BLK * (3 * sizeof(float) + 6 * sizeof(H));
+    static_assert(sizeof(H) == 2, "16-bit storage");
+    static constexpr int64_t BLOCK_BYTES = BLK * (3 * sizeof(float) + 3 * sizeof(uint32_t));
     __device__ static const float* cptr(const void* base, int64_t i) {
         return (const float*)((const unsigned char*)base + (i >> BLK_SHIFT) * BLOCK_BYTES) + (i & (BLK - 1));
     }
-    __device__ static const H* hptr(const void* base, int64_t i) {
-        return (const H*)((const unsigned char*)base + (i >> BLK_SHIFT) * BLOCK_BYTES + 3 * BLK * sizeof(float)) +
+    __device__ static const uint32_t* wptr(const void* base, int64_t i) {
+        return (const uint32_t*)((const unsigned char*)base + (i >> BLK_SHIFT) * BLOCK_BYTES + 3 * BLK * sizeof(float)) +
                (i & (BLK - 1));
     }
-    template <typename T, bool DEV>
-    __device__ static void load(const void* base, int64_t i, const InstParam& P, T* f) {
-        const float* c = cptr(base, i);
-        const H* h = hptr(base, i);
-        const float dr = c[0], jx = c[BLK], jy = c[2 * BLK];
+    // f of one cell from its stored moments and non-equilibrium words
+    template <typename T>
+    __device__ static void decode(float dr, float jx, float jy, const uint32_t* w, const InstParam& P, T* f) {
         const float rho = 1.0f + dr, ux = jx / rho, uy = jy / rho;
         float n[FVLBM_Q];
         float s = 0, sx = 0, sy = 0;
 #pragma unroll
         for (int a = 3; a < FVLBM_Q; a++) {
-            n[a] = h2f<H>(h[(a - 3) * BLK]) * P.inv_scale[a];
+            const uint32_t word = w[(a - 3) >> 1];
+            n[a] = h_value<H>(((a - 3) & 1) ? word >> 16 : word & 0xFFFFu) * P.inv_scale[a];
             s += n[a];
             sx += float(EXA(a)) * n[a];
             sy += float(EYA(a)) * n[a];
@@ -142,9 +151,16 @@ template <typename H> struct SplitIO {
         for (int a = 0; a < FVLBM_Q; a++) f[a] = (T)(feqs<float, true>(a, dr, ux, uy) + n[a]);
     }
     template <typename T, bool DEV>
+    __device__ static void load(const void* base, int64_t i, const InstParam& P, T* f) {
+        const float* c = cptr(base, i);
+        const uint32_t* wp = wptr(base, i);
+        const uint32_t w[3] = {wp[0], wp[BLK], wp[2 * BLK]};
+        decode<T>(c[0], c[BLK], c[2 * BLK], w, P, f);
+    }
+    template <typename T, bool DEV>
     __device__ static void store(void* base, int64_t i, const InstParam& P, const T* f) {
         float* c = (float*)cptr(base, i);
-        H* h = (H*)hptr(base, i);
+        uint32_t* wp = (uint32_t*)wptr(base, i);
         float dr = 0, jx = 0, jy = 0;
 #pragma unroll
         for (int a = 0; a < FVLBM_Q; a++) {
@@ -156,9 +172,12 @@ template <typename H> struct SplitIO {
         c[BLK] = jx;
         c[2 * BLK] = jy;
         const float rho = 1.0f + dr, ux = jx / rho, uy = jy / rho;
+        uint32_t bits[FVLBM_Q];
 #pragma unroll
         for (int a = 3; a < FVLBM_Q; a++)
-            h[(a - 3) * BLK] = f2h<H>(((float)f[a] - feqs<float, true>(a, dr, ux, uy)) * P.scale[a]);
+            bits[a] = h_bits<H>(((float)f[a] - feqs<float, true>(a, dr, ux, uy)) * P.scale[a]);
+#pragma unroll
+        for (int q = 0; q < 3; q++) wp[q * BLK] = bits[3 + 2 * q] | (bits[4 + 2 * q] << 16);
     }
     __device__ static void moments64(const void* base, int64_t i, const InstParam&, double& r, double& jx, double& jy) {
         const float* c = cptr(base, i);
@@ -166,7 +185,7 @@ template <typename H> struct SplitIO {
         jx = c[BLK];
         jy = c[2 * BLK];
     }
-    static constexpr size_t bytes_per_cell = 3 * sizeof(float) + 6 * sizeof(H);
+    static constexpr size_t bytes_per_cell = 3 * sizeof(float) + 3 * sizeof(uint32_t);
 };
 template <> struct CellIO<__half> : SplitIO<__half> {};
 template <> struct CellIO<__nv_bfloat16> : SplitIO<__nv_bfloat16> {};

@@ -328,20 +328,32 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
     const bool mine = l < nt;          // this thread owns tile cell l
     const int64_t gi = c0 + l;
 
-    // phase 1 (thread l's first local cell is local cell l)
+    // phase 1 (thread l's first local cell is local cell l).  The 16-bit split
+    // formats are staged raw (moments, packed non-equilibrium words, instance)
+    // in the face-table area, which is free until phase 2, and decoded after
+    // the barrier.
+    constexpr bool PLAIN = sizeof(S) == sizeof(T);
+    float* rawc = (float*)fvs;                     // [3][LS]
+    uint32_t* raww = (uint32_t*)(rawc + 3 * LS);   // [3][LS]
+    int32_t* rawg = (int32_t*)(raww + 3 * LS);     // [LS]
+    static_assert(PLAIN || 7 * LS * 4 <= (FVLBM_Q - 1) * FS * (int)sizeof(T), "raw staging fits the face table");
     int64_t gl = c0;
     for (int x = l; x < nt + nh; x += TILE) {
         const int64_t gx = x < nt ? c0 + x : (int64_t)v.halo[h0 + (x - nt)];
         if (x == l) gl = gx;
-        if constexpr (sizeof(S) == sizeof(T)) {
+        if constexpr (PLAIN) {
             const S* p = fin + blk_index(gx, FVLBM_Q);
 #pragma unroll
             for (int a = 0; a < FVLBM_Q; a++) cp_async_elem<T>(fs + a * LS + x, (const T*)p + a * BLK);
         } else {
-            T f[FVLBM_Q];
-            CellIO<S>::template load<T, DEV>(fin, gx, v.inst[v.grp[gx]], f);
+            const float* pc = CellIO<S>::cptr(fin, gx);
+            const uint32_t* pw = CellIO<S>::wptr(fin, gx);
 #pragma unroll
-            for (int a = 0; a < FVLBM_Q; a++) fs[a * LS + x] = f[a];
+            for (int q = 0; q < 3; q++) {
+                cp_async_elem<float>(rawc + q * LS + x, pc + q * BLK);
+                cp_async_elem<uint32_t>(raww + q * LS + x, pw + q * BLK);
+            }
+            cp_async_elem<int32_t>(rawg + x, v.grp + gx);
         }
     }
     // Phase 2 gives local cell x (tile cell, or 1-ring entry x - nt) to thread
@@ -369,6 +381,16 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
     }
     cp_async_wait_all();
     __syncthreads();
+    if constexpr (!PLAIN) {
+        for (int x = l; x < nt + nh; x += TILE) {
+            const uint32_t w[3] = {raww[x], raww[LS + x], raww[2 * LS + x]};
+            T f[FVLBM_Q];
+            CellIO<S>::template decode<T>(rawc[x], rawc[LS + x], rawc[2 * LS + x], w, v.inst[rawg[x]], f);
+#pragma unroll
+            for (int a = 0; a < FVLBM_Q; a++) fs[a * LS + x] = f[a];
+        }
+        __syncthreads();
+    }
 
     // phase 2
     auto item = [&](int x, int64_t g, const uint2* dx) {
