@@ -81,6 +81,17 @@ __device__ __forceinline__ T boundary_face(const Ghost<T>& g, bool out, int a, T
 template <typename T>
 __device__ __forceinline__ bool finite_val(T x) { return isfinite(x); }
 
+// rho, u of a cell for its boundary slots (ghost states); cells with interior
+// slots only do not need them before the collision.
+template <typename T, bool DEV, int MAXF>
+__device__ __forceinline__ void boundary_moments(const uint2* d, const T* f, T& rho, T& ux, T& uy) {
+    bool bc = false;
+#pragma unroll
+    for (int k = 0; k < MAXF; k++) bc |= (d[k].x & 0xFF) > SK_INTERIOR;
+    rho = ux = uy = T(0);
+    if (bc) moments<T, DEV>(f, rho, ux, uy);
+}
+
 // Least-squares gradient (Eq. leastsquare) of f_1..f_8 of one cell from the
 // differences to its stencil values.  d: the cell's slot descriptors;
 // fnb(k, fj) fills fj[1..8] with the neighbour values across interior slot k.
@@ -247,7 +258,7 @@ __global__ void __launch_bounds__(256) face_values_kernel(DevView v, const S* __
     T f[FVLBM_Q];
     CellIO<S>::template load<T, DEV>(fin, i, v.inst[v.grp[i]], f);
     T rho, ux, uy;
-    moments<T, DEV>(f, rho, ux, uy);
+    boundary_moments<T, DEV, MAXF>(d, f, rho, ux, uy);
     T gx[FVLBM_Q - 1], gy[FVLBM_Q - 1];
     lsq_gradient<T, DEV, MAXF>(d, G, v.bc, f, rho, ux, uy, gx, gy, [&](int k, T* fj) {
         const int64_t j = nb[k * BLK];
@@ -399,7 +410,7 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
 #pragma unroll
         for (int a = 0; a < FVLBM_Q; a++) f[a] = fs[a * LS + x];
         T rho, ux, uy;
-        moments<T, DEV>(f, rho, ux, uy);
+        boundary_moments<T, DEV, MAXF>(dx, f, rho, ux, uy);
         T gx[FVLBM_Q - 1], gy[FVLBM_Q - 1];
         lsq_gradient<T, DEV, MAXF>(dx, H, v.bc, f, rho, ux, uy, gx, gy, [&](int k, T* fj) {
             const T* p = fs + (dx[k].y & 0xFFFF);
@@ -425,7 +436,7 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
 #pragma unroll
         for (int a = 0; a < FVLBM_Q; a++) f[a] = fs[a * LS + x];
         T rho, ux, uy;
-        moments<T, DEV>(f, rho, ux, uy);
+        boundary_moments<T, DEV, MAXF>(dx, f, rho, ux, uy);
         T gx[FVLBM_Q - 1], gy[FVLBM_Q - 1];
         lsq_gradient<T, DEV, MAXF>(dx, H, v.bc, f, rho, ux, uy, gx, gy, [&](int k, T* fj) {
             const T* p = fs + (dx[k].y & 0xFFFF);
