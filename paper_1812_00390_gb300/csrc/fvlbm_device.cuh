@@ -133,7 +133,7 @@ template <typename H> struct SplitIO {
     // f of one cell from its stored moments and non-equilibrium words
     template <typename T>
     __device__ static void decode(float dr, float jx, float jy, const uint32_t* w, const InstParam& P, T* f) {
-        const float rho = 1.0f + dr, ux = jx / rho, uy = jy / rho;
+        const float inv_rho = 1.0f / (1.0f + dr), ux = jx * inv_rho, uy = jy * inv_rho;
         float n[FVLBM_Q];
         float s = 0, sx = 0, sy = 0;
 #pragma unroll
@@ -171,7 +171,7 @@ template <typename H> struct SplitIO {
         c[0] = dr;
         c[BLK] = jx;
         c[2 * BLK] = jy;
-        const float rho = 1.0f + dr, ux = jx / rho, uy = jy / rho;
+        const float inv_rho = 1.0f / (1.0f + dr), ux = jx * inv_rho, uy = jy * inv_rho;
         uint32_t bits[FVLBM_Q];
 #pragma unroll
         for (int a = 3; a < FVLBM_Q; a++)
