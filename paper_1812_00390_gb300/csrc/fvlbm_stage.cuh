@@ -67,17 +67,6 @@ __device__ __forceinline__ T ghost_delta(const Ghost<T>& g, int a, T fa, T fe) {
     return feqs<T, DEV>(a, g.r, g.ux, g.uy) - (g.sym ? fa : fe);
 }
 
-// Face value of direction a on a boundary face (Sec. 2.4.2): inlet / internal
-// outlet faces the cell flows out through: the reconstruction
-// f_i + grad f_i . r; otherwise the ghost value (half way for symmetry; the
-// cell value at an external outlet).
-template <typename T, bool DEV>
-__device__ __forceinline__ T boundary_face(const Ghost<T>& g, bool out, int a, T fa, T fe, T gxa, T gya, T rx, T ry) {
-    if (g.io && out) return fa + gxa * rx + gya * ry;
-    const T d = ghost_delta<T, DEV>(g, a, fa, fe);
-    return g.sym ? fa + T(0.5) * d : fa + d;
-}
-
 template <typename T>
 __device__ __forceinline__ bool finite_val(T x) { return isfinite(x); }
 
@@ -95,9 +84,13 @@ __device__ __forceinline__ void boundary_moments(const uint2* d, const T* f, T& 
 // Least-squares gradient (Eq. leastsquare) of f_1..f_8 of one cell from the
 // differences to its stencil values.  d: the cell's slot descriptors;
 // fnb(k, fj) fills fj[1..8] with the neighbour values across interior slot k.
-template <typename T, bool DEV, int MAXF, typename Geo, typename Nb>
+// On boundary slots it also writes the face values that are ghost values
+// (Sec. 2.4.2: all directions of walls, symmetry planes and external outlets,
+// inflow directions of inlets and internal outlets; half way to the ghost for
+// symmetry) into face(k) (stride `stride`; null: not written).
+template <typename T, bool DEV, int MAXF, typename Geo, typename Nb, typename Row>
 __device__ __forceinline__ void lsq_gradient(const uint2* d, const Geo& G, const BcParam* bcs, const T* f,
-                                             T rho, T ux, T uy, T* gx, T* gy, Nb fnb) {
+                                             T rho, T ux, T uy, T* gx, T* gy, Nb fnb, int64_t stride, Row face) {
 #pragma unroll
     for (int a = 0; a < FVLBM_Q - 1; a++) gx[a] = gy[a] = T(0);
 #pragma unroll
@@ -115,12 +108,18 @@ __device__ __forceinline__ void lsq_gradient(const uint2* d, const Geo& G, const
                 gy[a - 1] += c.y * dd;
             }
         } else {
+            // the ghost difference enters the gradient and, for every direction
+            // not reconstructed from the gradient, gives the face value at once
             const Ghost<T> g = ghost_state<T, DEV>(kind, bcs[d[k].x >> 16], rho, ux, uy, [&] { return G.nv(k); });
+            const uint32_t mask = (d[k].x >> 8) & 0xFF;
+            T* fo = face(k);
 #pragma unroll
             for (int a = 1; a < FVLBM_Q; a++) {
                 const T dd = ghost_delta<T, DEV>(g, a, f[a], feqs<T, DEV>(a, rho, ux, uy));
                 gx[a - 1] += c.x * dd;
                 gy[a - 1] += c.y * dd;
+                if (fo && !(g.io && ((mask >> (a - 1)) & 1u)))
+                    fo[(a - 1) * stride] = g.sym ? f[a] + T(0.5) * dd : f[a] + dd;
             }
         }
     }
@@ -128,8 +127,10 @@ __device__ __forceinline__ void lsq_gradient(const uint2* d, const Geo& G, const
 
 // Values of one cell on its faces (Eq. lslrflux, Sec. 2.4.2) into a face
 // table with direction stride `stride`: on interior faces the directions in
-// the slot's writer mask, on boundary faces every direction.  face(k) is the
-// slot's row in the table, or null to skip the slot.
+// the slot's writer mask; on inlet and internal-outlet faces the directions
+// the cell flows out through (the reconstruction f_i + grad f_i . r; every
+// other boundary face value is the ghost value, written by lsq_gradient).
+// face(k) is the slot's row in the table, or null to skip the slot.
 template <typename T, bool DEV, int MAXF, typename Geo, typename Row>
 __device__ __forceinline__ void write_faces(const uint2* d, const Geo& G, const BcParam* bcs, const T* f,
                                             T rho, T ux, T uy, const T* gx, const T* gy, int64_t stride, Row face) {
@@ -146,12 +147,14 @@ __device__ __forceinline__ void write_faces(const uint2* d, const Geo& G, const 
             for (int a = 1; a < FVLBM_Q; a++)
                 if (mask & (1u << (a - 1))) fo[(a - 1) * stride] = f[a] + gx[a - 1] * r.x + gy[a - 1] * r.y;
         } else {
-            const Ghost<T> g = ghost_state<T, DEV>(kind, bcs[d[k].x >> 16], rho, ux, uy, [&] { return G.nv(k); });
+            // inlet / internal outlet: directions the cell flows out through
+            // take the reconstruction (the others were written with the gradient)
+            const BcParam& b = bcs[d[k].x >> 16];
+            if (kind == SK_INLET || (kind == SK_OUTLET && !b.external)) {
 #pragma unroll
-            for (int a = 1; a < FVLBM_Q; a++)
-                fo[(a - 1) * stride] = boundary_face<T, DEV>(g, (mask >> (a - 1)) & 1u, a, f[a],
-                                                             feqs<T, DEV>(a, rho, ux, uy), gx[a - 1], gy[a - 1], r.x,
-                                                             r.y);
+                for (int a = 1; a < FVLBM_Q; a++)
+                    if ((mask >> (a - 1)) & 1u) fo[(a - 1) * stride] = f[a] + gx[a - 1] * r.x + gy[a - 1] * r.y;
+            }
         }
     }
 }
@@ -260,12 +263,13 @@ __global__ void __launch_bounds__(256) face_values_kernel(DevView v, const S* __
     T rho, ux, uy;
     boundary_moments<T, DEV, MAXF>(d, f, rho, ux, uy);
     T gx[FVLBM_Q - 1], gy[FVLBM_Q - 1];
+    T* fv = (T*)v.fv;
+    auto row = [&](int k) { return fv + d[k].y; };
     lsq_gradient<T, DEV, MAXF>(d, G, v.bc, f, rho, ux, uy, gx, gy, [&](int k, T* fj) {
         const int64_t j = nb[k * BLK];
         CellIO<S>::template load<T, DEV>(fin, j, v.inst[v.grp[j]], fj);
-    });
-    T* fv = (T*)v.fv;
-    write_faces<T, DEV, MAXF>(d, G, v.bc, f, rho, ux, uy, gx, gy, v.n_face, [&](int k) { return fv + d[k].y; });
+    }, v.n_face, row);
+    write_faces<T, DEV, MAXF>(d, G, v.bc, f, rho, ux, uy, gx, gy, v.n_face, row);
 }
 
 // Two-kernel stage, kernel 2 (Steps 4-5): flux sum over the cell's faces,
@@ -412,17 +416,18 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
         T rho, ux, uy;
         boundary_moments<T, DEV, MAXF>(dx, f, rho, ux, uy);
         T gx[FVLBM_Q - 1], gy[FVLBM_Q - 1];
+        // tile cells write every face; 1-ring entries only the faces they share
+        // with the tile (their other links hold no local face)
+        auto row = [&](int k) {
+            const uint32_t lf = dx[k].y >> 16;
+            return lf == LINK_NONE ? (T*)nullptr : fvs + lf;
+        };
         lsq_gradient<T, DEV, MAXF>(dx, H, v.bc, f, rho, ux, uy, gx, gy, [&](int k, T* fj) {
             const T* p = fs + (dx[k].y & 0xFFFF);
 #pragma unroll
             for (int a = 1; a < FVLBM_Q; a++) fj[a] = p[a * LS];
-        });
-        // tile cells write every face; 1-ring entries only the faces they share
-        // with the tile (their other links hold no local face)
-        write_faces<T, DEV, MAXF>(dx, H, v.bc, f, rho, ux, uy, gx, gy, FS, [&](int k) {
-            const uint32_t lf = dx[k].y >> 16;
-            return lf == LINK_NONE ? (T*)nullptr : fvs + lf;
-        });
+        }, FS, row);
+        write_faces<T, DEV, MAXF>(dx, H, v.bc, f, rho, ux, uy, gx, gy, FS, row);
     };
     if (l < n2) item(l, gl, d);
     // never taken while the planner keeps nt + n1 <= TILE: the staged
@@ -438,15 +443,18 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
         T rho, ux, uy;
         boundary_moments<T, DEV, MAXF>(dx, f, rho, ux, uy);
         T gx[FVLBM_Q - 1], gy[FVLBM_Q - 1];
+        // tile cells write every face; 1-ring entries only the faces they share
+        // with the tile (their other links hold no local face)
+        auto row = [&](int k) {
+            const uint32_t lf = dx[k].y >> 16;
+            return lf == LINK_NONE ? (T*)nullptr : fvs + lf;
+        };
         lsq_gradient<T, DEV, MAXF>(dx, H, v.bc, f, rho, ux, uy, gx, gy, [&](int k, T* fj) {
             const T* p = fs + (dx[k].y & 0xFFFF);
 #pragma unroll
             for (int a = 1; a < FVLBM_Q; a++) fj[a] = p[a * LS];
-        });
-        write_faces<T, DEV, MAXF>(dx, H, v.bc, f, rho, ux, uy, gx, gy, FS, [&](int k) {
-            const uint32_t lf = dx[k].y >> 16;
-            return lf == LINK_NONE ? (T*)nullptr : fvs + lf;
-        });
+        }, FS, row);
+        write_faces<T, DEV, MAXF>(dx, H, v.bc, f, rho, ux, uy, gx, gy, FS, row);
     }
     // phase 3 inputs, in flight during the wait
     T2 n[MAXF];
