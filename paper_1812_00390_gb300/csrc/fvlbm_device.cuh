@@ -100,6 +100,7 @@ template <typename S> struct PlainIO {
         }
     }
     static constexpr size_t bytes_per_cell = FVLBM_Q * sizeof(S);
+    static constexpr int64_t BLOCK_BYTES = (int64_t)FVLBM_Q * BLK * sizeof(S);
 };
 template <> struct CellIO<double> : PlainIO<double> {};
 template <> struct CellIO<float> : PlainIO<float> {};

@@ -138,6 +138,7 @@ struct DevView {
     int32_t strategy;        // STRATEGY_TWO_KERNEL or STRATEGY_TILE
     int32_t block;           // threads per block of the two-kernel stage
     int32_t tile;            // most cells per tile (threads per CTA)
+    int32_t sms;             // streaming multiprocessors of the device
     int64_t n_tiles;
     const int64_t* tile_begin; // [n_tiles + 1] first cell of each tile
     const int64_t* halo_ptr;   // [n_tiles + 1] into halo

@@ -672,6 +672,7 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
     v.block = L.block;
     if (L.strategy == STRATEGY_TILE) {
         v.tile = L.tp.tile;
+        v.sms = device_sms(p0.device);
         v.n_tiles = L.tp.n_tiles;
         v.tile_begin = (const int64_t*)(base + L.off_tbegin);
         v.halo_ptr = (const int64_t*)(base + L.off_hptr);

@@ -191,6 +191,10 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
     else
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
 }
+// Hint: bring a 16-byte aligned range (a multiple of 16 bytes) into L2.
+__device__ __forceinline__ void prefetch_l2(const void* p, int64_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"((uint32_t)bytes) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 template <typename V>
 __device__ __forceinline__ void cp_async_vec(V* dst, const V* src) {
@@ -324,7 +328,7 @@ __global__ void __launch_bounds__(256) update_kernel(DevView v, const S* __restr
 template <typename T, typename S, int MAXF, bool DEV, int TILE>
 __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0 ? (sizeof(T) == 4 ? 1024 : 512) / TILE : 1)
     stage_tile_kernel(DevView v, const S* __restrict__ fin,
-                                                          const S* fbase, S* fout, T beta, int mode) {
+                                                          const S* fbase, S* fout, T beta, int mode, int pf) {
     constexpr int LS = TileDims<TILE, MAXF, sizeof(T)>::LS;
     constexpr int FS = TileDims<TILE, MAXF, sizeof(T)>::FS;
     typedef typename Vec2<T>::type T2;
@@ -340,6 +344,21 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
     const int64_t q0 = v.r1_ptr[t];
     const int n1 = (int)(v.r1_ptr[t + 1] - q0);
     const int l = threadIdx.x;
+    // The CTA that starts when this one ends works on about tile t + pf (pf =
+    // CTAs resident on the GPU): bring that tile's state and geometry into L2
+    // now, so that its staging reads L2 rather than HBM.
+    if (l == 0 && pf > 0 && t + pf < v.n_tiles) {
+        const int64_t tp = t + pf;
+        const int64_t b0 = v.tile_begin[tp] >> BLK_SHIFT;
+        const int64_t nb = ((v.tile_begin[tp + 1] + BLK - 1) >> BLK_SHIFT) - b0;
+        constexpr int64_t SB = CellIO<S>::BLOCK_BYTES;
+        constexpr int64_t DB = (int64_t)MAXF * BLK * sizeof(uint2);
+        constexpr int64_t GB = (int64_t)3 * MAXF * BLK * sizeof(T2);
+        prefetch_l2((const unsigned char*)fin + b0 * SB, nb * SB);
+        if (mode == MODE_RK && fbase != fin) prefetch_l2((const unsigned char*)fbase + b0 * SB, nb * SB);
+        prefetch_l2((const unsigned char*)v.desc + b0 * DB, nb * DB);
+        prefetch_l2((const unsigned char*)v.geo + b0 * GB, nb * GB);
+    }
     const bool mine = l < nt;          // this thread owns tile cell l
     const int64_t gi = c0 + l;
 
@@ -504,7 +523,16 @@ static int tile_launch(const DevView& v, cudaStream_t st, const void* fin, const
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return fail(FVLBM_ERR_CUDA, "fused stage: %zu B shared memory: %s", smem, cudaGetErrorString(e));
     }
-    kern<<<(unsigned)v.n_tiles, TILE, smem, st>>>(v, (const S*)fin, (const S*)fbase, (S*)fout, (T)beta, mode);
+    // prefetch distance: the CTAs that fit on the GPU at once (queried once per kernel)
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE, smem) != cudaSuccess) {
+            cudaGetLastError();
+            per_sm = 0;
+        }
+    }
+    const int pf = per_sm * v.sms;
+    kern<<<(unsigned)v.n_tiles, TILE, smem, st>>>(v, (const S*)fin, (const S*)fbase, (S*)fout, (T)beta, mode, pf);
     return FVLBM_OK;
 }
 
