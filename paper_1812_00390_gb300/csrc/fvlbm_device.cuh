@@ -38,13 +38,17 @@ __device__ __forceinline__ void moments(const T* f, T& r, T& ux, T& uy) {
 
 // Eq. (feq).  FP64 mode: r = rho, returns f^eq.  Deviation mode: r = rho - 1,
 // returns f^eq - w = w [(rho - 1) + rho (3 e.u + 4.5 (e.u)^2 - 1.5 u^2)].
+// The polynomial is evaluated as e.u (3 + 4.5 e.u) - 1.5 u^2 (two fused
+// multiply-adds per direction once u^2 is known).
 template <typename T, bool DEV>
 __device__ __forceinline__ T feqs(int a, T r, T ux, T uy) {
-    T eu = T(EXA(a)) * ux + T(EYA(a)) * uy;
-    T uu = ux * ux + uy * uy;
-    T poly = T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu;
-    if (DEV) return wgt<T>(a) * (r + (T(1) + r) * poly);
-    return r * wgt<T>(a) * (T(1) + poly);
+    const T eu = T(EXA(a)) * ux + T(EYA(a)) * uy;
+    const T uu15 = T(1.5) * (ux * ux + uy * uy);
+    if (DEV) {
+        const T poly = fma(eu, fma(T(4.5), eu, T(3)), -uu15);
+        return wgt<T>(a) * fma(T(1) + r, poly, r);
+    }
+    return r * wgt<T>(a) * fma(eu, fma(T(4.5), eu, T(3)), T(1) - uu15);
 }
 
 // Density argument of feqs for a given density.
