@@ -222,7 +222,7 @@ template <typename T, int MAXF, int STRIDE> struct StagedGeo {
 // (f - f^eq) / tau, then out = base + beta dt rhs (multistage; the base state
 // is fb when use_fb, else f itself) or the AB2 combination.  Returns false
 // when an output is not finite.
-template <typename T, typename S, bool DEV>
+template <typename T, typename S, bool DEV, bool FMA_RK = false>
 __device__ __forceinline__ bool update_cell(const DevView& v, const InstParam& P, int64_t i, const T* f, T rho, T ux,
                                             T uy, const T* flux, const T* fb, bool use_fb, S* fout, T beta,
                                             int mode) {
@@ -231,6 +231,20 @@ __device__ __forceinline__ bool update_cell(const DevView& v, const InstParam& P
     bool bad = false;
     T* rp = (T*)v.rprev;
     T out[FVLBM_Q];
+    if constexpr (FMA_RK) {
+        if (mode == MODE_RK) {
+            // base + beta dt rhs = base - c1 flux + c2 (f^eq - f), c1 = beta dt,
+            // c2 = beta dt / tau: fewer FP64 operations
+            const T c1 = beta * dt, c2 = c1 * inv_tau;
+#pragma unroll
+            for (int a = 0; a < FVLBM_Q; a++) {
+                out[a] = fma(c2, feqs<T, DEV>(a, rho, ux, uy) - f[a], fma(-c1, flux[a], use_fb ? fb[a] : f[a]));
+                bad |= !finite_val(out[a]);
+            }
+            CellIO<S>::template store<T, DEV>(fout, i, P, out);
+            return !bad;
+        }
+    }
 #pragma unroll
     for (int a = 0; a < FVLBM_Q; a++) {
         const T rhs = -flux[a] - (f[a] - feqs<T, DEV>(a, rho, ux, uy)) * inv_tau;
@@ -306,7 +320,8 @@ __global__ void __launch_bounds__(256) update_kernel(DevView v, const S* __restr
     T fb[FVLBM_Q];
     const bool rk_base = mode == MODE_RK && fbase != fin;
     if (rk_base) CellIO<S>::template load<T, DEV>(fbase, i, P, fb);
-    if (!update_cell<T, S, DEV>(v, P, i, f, rho, ux, uy, flux, fb, rk_base, fout, beta, mode))
+    // the FP64 two-kernel stage is bound by the FP64 units: the shorter multistage form
+    if (!update_cell<T, S, DEV, sizeof(T) == 8>(v, P, i, f, rho, ux, uy, flux, fb, rk_base, fout, beta, mode))
         *v.flag = 1;
 }
 
