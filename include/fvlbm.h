@@ -107,9 +107,15 @@ typedef struct fvlbm_params {
     double rho0;       /* initial density (Step 0: f = f^eq(rho0, u0)) */
     double u0[2];      /* initial velocity */
     int32_t device;    /* CUDA device ordinal; equal for all instances */
-    int32_t kernel;    /* stage kernel: 0 = automatic; 1 = two kernels per stage (face
-                          values through memory); 128, 256, 512 or 1024 = one fused kernel
-                          per stage with that many cells per tile; equal for all instances */
+    int32_t kernel;    /* stage kernel: 0 = automatic (FP64: two kernels; otherwise fused
+                          512-thread tiles when the mesh fills the GPU, smaller tiles or two
+                          kernels for small meshes); 1 = two kernels per stage (face values
+                          through memory); 128, 256, 512 or 1024 = one fused kernel per stage
+                          with CTAs of that many threads (a tile holds at most that many
+                          cells and 1-ring cells together).  Tile sizes whose shared memory
+                          exceeds a CTA's (FP64: 1024; FP64 meshes with cells of more than 4
+                          faces: 512 and 1024; FP32/16-bit meshes with cells of more than 4
+                          faces: 1024) give FVLBM_ERR_UNSUPPORTED.  Equal for all instances. */
 } fvlbm_params;
 
 typedef struct fvlbm_mesh_info_s {
