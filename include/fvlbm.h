@@ -273,6 +273,11 @@ int fvlbm_set_f(fvlbm_solver* s, const double* f);
 typedef enum fvlbm_host_mode { FVLBM_HOST_AUTO = 0, FVLBM_HOST_STAGED = 1 } fvlbm_host_mode;
 int fvlbm_host_transfer(fvlbm_solver* s, int32_t mode, int32_t* direct);
 
+/* The stage kernel the solver runs (the choice params.kernel = 0 resolved to):
+ * 1 for the two-kernel stage, else the fused stage's threads per CTA.
+ * kernel: host, written.  Errors: FVLBM_ERR_ARG. */
+int fvlbm_stage_kernel(const fvlbm_solver* s, int32_t* kernel);
+
 /* Wait for the solver's stream; reports FVLBM_ERR_DIVERGED if flagged. */
 int fvlbm_sync(fvlbm_solver* s);
 

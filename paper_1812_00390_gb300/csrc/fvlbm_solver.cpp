@@ -1033,6 +1033,13 @@ extern "C" int fvlbm_set_f(fvlbm_solver* s, const double* f) {
     return FVLBM_OK;
 }
 
+extern "C" int fvlbm_stage_kernel(const fvlbm_solver* s, int32_t* kernel) {
+    clear_error();
+    if (!s || !kernel) return fail(FVLBM_ERR_ARG, "fvlbm_stage_kernel: null argument");
+    *kernel = s->v.strategy == STRATEGY_TILE ? s->v.tile : 1;
+    return FVLBM_OK;
+}
+
 extern "C" int fvlbm_host_transfer(fvlbm_solver* s, int32_t mode, int32_t* direct) {
     clear_error();
     if (!s || (mode != FVLBM_HOST_AUTO && mode != FVLBM_HOST_STAGED))

@@ -72,7 +72,7 @@ class ServerStatsT(C.Structure):
 #: every symbol include/fvlbm.h declares
 EXPORTS = ["fvlbm_mesh_create", "fvlbm_mesh_concat", "fvlbm_mesh_destroy", "fvlbm_mesh_info",
            "fvlbm_suggest_dt", "fvlbm_workspace_bytes", "fvlbm_init", "fvlbm_step", "fvlbm_macros",
-           "fvlbm_residual", "fvlbm_mass", "fvlbm_mass_noalloc", "fvlbm_get_f", "fvlbm_set_f", "fvlbm_host_transfer", "fvlbm_sync",
+           "fvlbm_residual", "fvlbm_mass", "fvlbm_mass_noalloc", "fvlbm_get_f", "fvlbm_set_f", "fvlbm_host_transfer", "fvlbm_stage_kernel", "fvlbm_sync",
            "fvlbm_get_dt", "fvlbm_profile", "fvlbm_autotune", "fvlbm_fma_peak", "fvlbm_launches_per_step", "fvlbm_solver_destroy",
            "fvlbm_server_create", "fvlbm_server_submit", "fvlbm_server_poll", "fvlbm_server_request",
            "fvlbm_server_stats", "fvlbm_server_destroy", "fvlbm_last_error"]
@@ -111,6 +111,7 @@ def _load():
         "fvlbm_autotune": [P, C.POINTER(ParamsT), C.c_int32, P, C.c_int32, i32p, dp],
         "fvlbm_fma_peak": [C.c_int32, C.c_int32, dp],
         "fvlbm_host_transfer": [P, C.c_int32, i32p],
+        "fvlbm_stage_kernel": [P, i32p],
         "fvlbm_solver_destroy": [P],
         "fvlbm_server_create": [C.POINTER(ServerConfigT), PP],
         "fvlbm_server_submit": [P, P, C.POINTER(ParamsT), C.c_int32, i64p],
@@ -295,6 +296,12 @@ class Solver:
     def set_f(self, f):
         f = np.ascontiguousarray(f, np.float64).reshape(self.n_cell, 9)
         _check(lib.fvlbm_set_f(self._h, _d(f)))
+
+    def stage_kernel(self) -> int:
+        """1 for the two-kernel stage, else the fused stage's threads per CTA."""
+        k = C.c_int32()
+        _check(lib.fvlbm_stage_kernel(self._h, C.byref(k)))
+        return k.value
 
     def host_transfer(self, mode: str = "auto") -> bool:
         """How get_f / set_f / macros reach host buffers: "auto" (direct device

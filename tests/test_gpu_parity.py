@@ -388,5 +388,9 @@ def test_autotune_picks_a_variant(fv):
     assert best in fv.KERNEL_VARIANTS
     assert ms[best] == min(ms.values()) and np.isfinite(ms[best]) and ms[best] > 0
     s = fv.Solver(fv.Mesh(m), fv.make_params(0.05, scheme="rk2", precision="fp32", kernel=best))
+    assert s.stage_kernel() == best
     s.step(3)
     s.sync()
+    # the automatic choice resolves to one of the variants: FP64 to the two-kernel stage
+    assert fv.Solver(fv.Mesh(m), fv.make_params(0.05, precision="fp32")).stage_kernel() in fv.KERNEL_VARIANTS
+    assert fv.Solver(fv.Mesh(m), fv.make_params(0.05, precision="fp64")).stage_kernel() == 1
