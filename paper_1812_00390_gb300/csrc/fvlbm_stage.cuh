@@ -373,6 +373,14 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
         if (mode == MODE_RK && fbase != fin) prefetch_l2((const unsigned char*)fbase + b0 * SB, nb * SB);
         prefetch_l2((const unsigned char*)v.desc + b0 * DB, nb * DB);
         prefetch_l2((const unsigned char*)v.geo + b0 * GB, nb * GB);
+        // its halo list and 1-ring links (16-byte aligned cover of each range)
+        auto range = [&](const void* base, int64_t begin, int64_t end) {
+            const int64_t a = begin & ~(int64_t)15, e = (end + 15) & ~(int64_t)15;
+            if (e > a) prefetch_l2((const unsigned char*)base + a, e - a);
+        };
+        range(v.halo, 4 * v.halo_ptr[tp], 4 * v.halo_ptr[tp + 1]);
+        constexpr int64_t LB = (int64_t)MAXF * BLK * 4;   // bytes per block of 32 entries
+        range(v.r1link, (v.r1_ptr[tp] >> BLK_SHIFT) * LB, ((v.r1_ptr[tp + 1] + BLK - 1) >> BLK_SHIFT) * LB);
     }
     const bool mine = l < nt;          // this thread owns tile cell l
     const int64_t gi = c0 + l;
