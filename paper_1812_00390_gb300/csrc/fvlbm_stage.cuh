@@ -379,6 +379,7 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
             if (e > a) prefetch_l2((const unsigned char*)base + a, e - a);
         };
         range(v.halo, 4 * v.halo_ptr[tp], 4 * v.halo_ptr[tp + 1]);
+        range(v.grp, 4 * v.tile_begin[tp], 4 * v.tile_begin[tp + 1]);   // instance ids
         constexpr int64_t LB = (int64_t)MAXF * BLK * 4;   // bytes per block of 32 entries
         range(v.r1link, (v.r1_ptr[tp] >> BLK_SHIFT) * LB, ((v.r1_ptr[tp + 1] + BLK - 1) >> BLK_SHIFT) * LB);
     }
