@@ -359,30 +359,6 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
     const int64_t q0 = v.r1_ptr[t];
     const int n1 = (int)(v.r1_ptr[t + 1] - q0);
     const int l = threadIdx.x;
-    // The CTA that starts when this one ends works on about tile t + pf (pf =
-    // CTAs resident on the GPU): bring that tile's state and geometry into L2
-    // now, so that its staging reads L2 rather than HBM.
-    if (l == 0 && pf > 0 && t + pf < v.n_tiles) {
-        const int64_t tp = t + pf;
-        const int64_t b0 = v.tile_begin[tp] >> BLK_SHIFT;
-        const int64_t nb = ((v.tile_begin[tp + 1] + BLK - 1) >> BLK_SHIFT) - b0;
-        constexpr int64_t SB = CellIO<S>::BLOCK_BYTES;
-        constexpr int64_t DB = (int64_t)MAXF * BLK * sizeof(uint2);
-        constexpr int64_t GB = (int64_t)3 * MAXF * BLK * sizeof(T2);
-        prefetch_l2((const unsigned char*)fin + b0 * SB, nb * SB);
-        if (mode == MODE_RK && fbase != fin) prefetch_l2((const unsigned char*)fbase + b0 * SB, nb * SB);
-        prefetch_l2((const unsigned char*)v.desc + b0 * DB, nb * DB);
-        prefetch_l2((const unsigned char*)v.geo + b0 * GB, nb * GB);
-        // its halo list and 1-ring links (16-byte aligned cover of each range)
-        auto range = [&](const void* base, int64_t begin, int64_t end) {
-            const int64_t a = begin & ~(int64_t)15, e = (end + 15) & ~(int64_t)15;
-            if (e > a) prefetch_l2((const unsigned char*)base + a, e - a);
-        };
-        range(v.halo, 4 * v.halo_ptr[tp], 4 * v.halo_ptr[tp + 1]);
-        range(v.grp, 4 * v.tile_begin[tp], 4 * v.tile_begin[tp + 1]);   // instance ids
-        constexpr int64_t LB = (int64_t)MAXF * BLK * 4;   // bytes per block of 32 entries
-        range(v.r1link, (v.r1_ptr[tp] >> BLK_SHIFT) * LB, ((v.r1_ptr[tp + 1] + BLK - 1) >> BLK_SHIFT) * LB);
-    }
     const bool mine = l < nt;          // this thread owns tile cell l
     const int64_t gi = c0 + l;
 
@@ -436,6 +412,32 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
             cp_async_vec<T2>(gst + k * TILE + l, &H.g[(3 * k) * BLK]);
             cp_async_vec<T2>(gst + (MAXF + k) * TILE + l, &H.g[(3 * k + 1) * BLK]);
         }
+    }
+    // The CTA that starts when this one ends works on about tile t + pf (pf =
+    // CTAs resident on the GPU): bring that tile's state and geometry into L2
+    // now, so that its staging reads L2 rather than HBM.  The last thread does
+    // it once its own copies are in flight, so that the loads of the other
+    // tile's bounds overlap them.
+    if (l == TILE - 1 && pf > 0 && t + pf < v.n_tiles) {
+        const int64_t tp = t + pf;
+        const int64_t b0 = v.tile_begin[tp] >> BLK_SHIFT;
+        const int64_t nb = ((v.tile_begin[tp + 1] + BLK - 1) >> BLK_SHIFT) - b0;
+        constexpr int64_t SB = CellIO<S>::BLOCK_BYTES;
+        constexpr int64_t DB = (int64_t)MAXF * BLK * sizeof(uint2);
+        constexpr int64_t GB = (int64_t)3 * MAXF * BLK * sizeof(T2);
+        prefetch_l2((const unsigned char*)fin + b0 * SB, nb * SB);
+        if (mode == MODE_RK && fbase != fin) prefetch_l2((const unsigned char*)fbase + b0 * SB, nb * SB);
+        prefetch_l2((const unsigned char*)v.desc + b0 * DB, nb * DB);
+        prefetch_l2((const unsigned char*)v.geo + b0 * GB, nb * GB);
+        // its halo list and 1-ring links (16-byte aligned cover of each range)
+        auto range = [&](const void* base, int64_t begin, int64_t end) {
+            const int64_t a = begin & ~(int64_t)15, e = (end + 15) & ~(int64_t)15;
+            if (e > a) prefetch_l2((const unsigned char*)base + a, e - a);
+        };
+        range(v.halo, 4 * v.halo_ptr[tp], 4 * v.halo_ptr[tp + 1]);
+        range(v.grp, 4 * v.tile_begin[tp], 4 * v.tile_begin[tp + 1]);   // instance ids
+        constexpr int64_t LB = (int64_t)MAXF * BLK * 4;   // bytes per block of 32 entries
+        range(v.r1link, (v.r1_ptr[tp] >> BLK_SHIFT) * LB, ((v.r1_ptr[tp + 1] + BLK - 1) >> BLK_SHIFT) * LB);
     }
     cp_async_wait_all();
     __syncthreads();
