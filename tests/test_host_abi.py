@@ -102,3 +102,31 @@ def test_init_without_gpu_fails_loudly(fv):
     with pytest.raises(fv.FvlbmError) as e:
         fv.Solver(h, fv.make_params(0.24), stream=0, use_torch_workspace=False)
     assert e.value.name == "UNSUPPORTED"
+
+
+def test_stage_kernel_capacity_on_the_host(fv):
+    """The layout and the fused stage's tile plan are built on the host: every
+    variant that fits a CTA's shared memory gives a workspace; the tile sizes
+    that would not fit (FP64 1024-thread tiles, FP64 hexagon tiles of 512,
+    hexagon tiles of 1024) are refused with FVLBM_ERR_UNSUPPORTED."""
+    def ws(mesh, prec, kernel):
+        arr = (fv.ParamsT * 1)(fv.make_params(0.1, scheme="rk2", precision=prec, kernel=kernel))
+        n = C.c_size_t()
+        rc = fv.lib.fvlbm_workspace_bytes(mesh._h, arr, 1, C.byref(n))
+        return fv.ERRORS.get(rc, rc) if rc else "OK", n.value
+
+    quads, hexes = fv.Mesh(mg.cavity(40, 5.0)), fv.Mesh(mg.bricks(20, 16))   # handles kept alive
+    for prec in ("fp32", "fp16", "bf16", "fp64"):
+        sizes = {}
+        for k in (1, 128, 256, 512):
+            rc, n = ws(quads, prec, k)
+            assert rc == "OK" and n > 0, (prec, k, rc)
+            sizes[k] = n
+        # the fused stage keeps no face-value table in memory
+        assert sizes[512] < sizes[1]
+    assert ws(quads, "fp32", 1024)[0] == "OK"
+    assert ws(quads, "fp64", 1024)[0] == "UNSUPPORTED"
+    assert ws(hexes, "fp64", 256)[0] == "OK"
+    assert ws(hexes, "fp64", 512)[0] == "UNSUPPORTED"
+    assert ws(hexes, "fp32", 1024)[0] == "UNSUPPORTED"
+    assert ws(quads, "fp32", 384)[0] == "ARG"
