@@ -258,18 +258,25 @@ def measured_peaks():
 
 
 def kernel_source_sha() -> str:
-    """Hash of the sources that decide what the stage kernels do and read: the
-    kernels and the device storage (whole files), the shared-memory capacities
-    and the host-side tile planner (their sections of the other files)."""
+    """Hash of the code (comments and blank space stripped) that decides what
+    the stage kernels do and read: the kernels and the device storage (whole
+    files), the shared-memory capacities and the host-side tile planner (their
+    sections of the other files)."""
     csrc = os.path.join(ROOT, "paper_1812_00390_gb300", "csrc")
+
+    def code(txt):
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        txt = re.sub(r"//[^\n]*", "", txt)
+        return re.sub(r"\s+", " ", txt).strip()
+
     h = hashlib.sha256()
     for f in ("fvlbm_stage.cuh", "fvlbm_device.cuh"):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        h.update(code(open(os.path.join(csrc, f)).read()).encode())
     for f, begin, end in (("fvlbm_internal.h", "struct TileDims", "};"),
                           ("fvlbm_solver.cpp", "struct TilePlan {", "// Offsets of every array")):
         txt = open(os.path.join(csrc, f)).read()
         a = txt.index(begin)
-        h.update(txt[a:txt.index(end, a)].encode())
+        h.update(code(txt[a:txt.index(end, a)]).encode())
     return h.hexdigest()[:16]
 
 

@@ -325,25 +325,29 @@ __global__ void __launch_bounds__(256) update_kernel(DevView v, const S* __restr
         *v.flag = 1;
 }
 
-// Fused stage: one CTA per tile of at most TILE consecutive cells (Hilbert
-// order), everything between the state read and the state write in shared
-// memory:
-//   phase 1  f of the tile, its 1-ring and its 2-ring (cp.async when the
-//            stored type is the arithmetic type)
-//   phase 2  per tile and 1-ring cell (one per thread): the gradient (Eq. leastsquare), then
-//            its values on the tile's faces (Eq. lslrflux / Sec. 2.4.2): on
-//            interior faces the directions it writes (upwind side), on
-//            boundary faces (tile cells) every direction -- one writer per
-//            (face, direction), into a table of the tile's faces
+// Fused stage: one CTA per tile of consecutive cells (Hilbert order; tile
+// and 1-ring together at most TILE cells), everything between the state read
+// and the state write in shared memory:
+//   phase 1  cp.async of the state of the tile, its 1-ring and its 2-ring
+//            (the 16-bit formats raw, decoded after the barrier), and of the
+//            least-squares and reconstruction vectors of each thread's
+//            gradient cell; its slot descriptors into registers
+//   phase 2  per tile and 1-ring cell (one per thread): the gradient
+//            (Eq. leastsquare) and its values on the tile's faces
+//            (Eq. lslrflux / Sec. 2.4.2): on interior faces the directions it
+//            writes (upwind side), on boundary faces (tile cells) every
+//            direction -- one writer per (face, direction), into a table of
+//            the tile's faces
 //   phase 3  per tile cell: flux sum from the face table, collision and the
 //            time update (Eq. rhs, Sec. 2.3)
 // The global loads of each phase are issued before the barrier that precedes
-// it, so that their latency overlaps the wait.  Shared-memory strides are
-// compile-time constants (TileDims); the planner keeps every tile within them.
+// it, so that their latency overlaps the wait, and each CTA prefetches into L2
+// the data of a tile that starts about one CTA lifetime later (pf = resident
+// CTAs ahead).  Shared-memory strides are compile-time constants (TileDims);
+// the planner keeps every tile within them.
 template <typename T, typename S, int MAXF, bool DEV, int TILE>
 __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0 ? (sizeof(T) == 4 ? 1024 : 512) / TILE : 1)
-    stage_tile_kernel(DevView v, const S* __restrict__ fin,
-                                                          const S* fbase, S* fout, T beta, int mode, int pf) {
+    stage_tile_kernel(DevView v, const S* __restrict__ fin, const S* fbase, S* fout, T beta, int mode, int pf) {
     constexpr int LS = TileDims<TILE, MAXF, sizeof(T)>::LS;
     constexpr int FS = TileDims<TILE, MAXF, sizeof(T)>::FS;
     typedef typename Vec2<T>::type T2;
