@@ -181,11 +181,14 @@ bool try_tile(const Mesh& M, int maxf, int64_t c0, int len, int threads, int ls,
     W.t_f.assign((size_t)len * maxf, -1);
     W.r_nb.assign((size_t)n1 * maxf, -1);
     W.r_f.assign((size_t)n1 * maxf, -1);
+    // faces numbered slot by slot (all cells' slot 0, then slot 1, ...): the
+    // cells of a warp then reach their slot-k faces at mostly consecutive
+    // indices, which spreads their face-table accesses over the memory banks
     int nf = 0;
-    for (int li = 0; li < len; li++) {
-        const int64_t i = c0 + li;
-        const int64_t c = M.perm[i];
-        for (int k = 0; k < M.nf[c]; k++) {
+    for (int k = 0; k < maxf; k++) {
+        for (int li = 0; li < len; li++) {
+            const int64_t c = M.perm[c0 + li];
+            if (k >= M.nf[c]) continue;
             const Slot& S = M.slots[(size_t)c * MAXP + k];
             const size_t x = (size_t)li * maxf + k;
             if (S.kind == SK_INTERIOR) {
