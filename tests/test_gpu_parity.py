@@ -164,6 +164,27 @@ def test_fused_single_stage_many_tiles(fv, scheme):
     assert rel_err(got.get_f(), ref.get_f()) < 1e-6
 
 
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("scheme", ["euler", "ab2", "rk4"])
+def test_fused_stage_16bit_formats(fv, orc, prec, scheme):
+    """The 16-bit split formats through the fused stage (raw staging and decode
+    in shared memory; alternating state for Euler / AB2) agree with the
+    two-kernel stage, which decodes the same storage from global memory."""
+    m = MESHES["cylinder"]()
+    tau = 0.15
+    dt = orc.Oracle(m).cfl_dt(0.5, 0.1, tau, scheme)
+    f0 = f_random(orc, m, seed=29, noise=0.01)
+    out = []
+    for kernel in (1, 128):
+        s = fv.Solver(fv.Mesh(m), fv.make_params(tau, dt=dt, scheme=scheme, precision=prec, kernel=kernel))
+        s.set_f(f0)
+        for n in (1, 33, 2):
+            s.step(n)
+        out.append(s.get_f())
+        s.close()
+    assert rel_err(out[1], out[0]) < 1e-5
+
+
 def test_fused_tiles_span_instances(fv):
     """Tiles that straddle instance boundaries give the same state as the
     two-kernel stage (instances of 2 to 3750 cells, tiles of up to 256 cells:
