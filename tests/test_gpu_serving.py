@@ -28,7 +28,7 @@ def _meshes():
             mg.cylinder_hybrid(n_rad=8, n_circ=32, first=0.02, growth=1.2, r_far=6.0, n_tri_rings=8, seed=4)]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "fp16"])
 def test_each_result_same_alone_and_in_the_mix(fv, prec):
     meshes = _meshes()
     taus = [0.01, 0.012, 0.05, 0.24, 0.015, 0.02]
