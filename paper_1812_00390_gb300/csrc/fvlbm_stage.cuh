@@ -553,14 +553,17 @@ static int tile_launch(const DevView& v, cudaStream_t st, const void* fin, const
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return fail(FVLBM_ERR_CUDA, "fused stage: %zu B shared memory: %s", smem, cudaGetErrorString(e));
     }
-    // prefetch distance: the CTAs that fit on the GPU at once (queried once per kernel)
-    static int per_sm = -1;
-    if (per_sm < 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE, smem) != cudaSuccess) {
+    // prefetch distance: the CTAs that fit on the GPU at once (queried once per
+    // kernel; a function-local static is initialised once even when several
+    // host threads launch at the same time)
+    static const int per_sm = [&] {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, TILE, smem) != cudaSuccess) {
             cudaGetLastError();
-            per_sm = 0;
+            n = 0;
         }
-    }
+        return n;
+    }();
     const int pf = per_sm * v.sms;
     kern<<<(unsigned)v.n_tiles, TILE, smem, st>>>(v, (const S*)fin, (const S*)fbase, (S*)fout, (T)beta, mode, pf);
     return FVLBM_OK;
