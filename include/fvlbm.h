@@ -262,8 +262,9 @@ int fvlbm_set_f(fvlbm_solver* s, const double* f);
  *     Grace host's memory over NVLink-C2C), the kernels read and write the
  *     caller's buffer directly, in the caller's cell order: no host-side
  *     reordering, no staging copy.  Otherwise as FVLBM_HOST_STAGED.
- *   FVLBM_HOST_STAGED: the library reorders on the host and copies through a
- *     staging buffer of its own.
+ *   FVLBM_HOST_STAGED: one copy between the caller's buffer and a device
+ *     staging buffer in the workspace (caller order); the kernels reorder on
+ *     the device.
  * The buffers passed to those calls must be ordinary host memory (malloc,
  * numpy, pinned) or device memory; the calls synchronise before returning, so
  * the caller may reuse them at once.  The results are bitwise the same in both

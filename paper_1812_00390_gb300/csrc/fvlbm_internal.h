@@ -129,7 +129,7 @@ struct DevView {
     double* uold;   // [2][np]
     double* part;   // [n_chunk][3] block partial sums
     double* red;    // [n_inst][3]  per-instance sums
-    double* conv;   // [9][np] FP64 staging for get/set of f
+    double* conv;   // [9][np] doubles: device staging of get_f / set_f / macros in caller order
     const int64_t* chunk;   // [n_chunk][3] (begin, end, instance)
     int64_t n_chunk;
     int32_t* flag;  // non-finite flag
@@ -169,11 +169,8 @@ int stage_bf16(const DevView& v, void* stream, const void* fin, const void* fbas
                void* const* ev);
 int launch_macros(const DevView& v, int prec, void* stream);
 int launch_reduce(const DevView& v, void* stream, int what);
-int launch_get_f(const DevView& v, int prec, void* stream);
-int launch_set_f(const DevView& v, int prec, void* stream);
-// The same, and the macros, on a caller's buffer in the caller's cell order
-// that the device accesses directly (host memory reachable by the GPU, or
-// device memory).
+// f and the macros in the caller's cell order, in a buffer the device
+// accesses (host memory reachable by the GPU, or device memory).
 int launch_get_f_direct(const DevView& v, int prec, void* stream, double* f);
 int launch_set_f_direct(const DevView& v, int prec, void* stream, const double* f);
 int launch_macros_direct(const DevView& v, int prec, void* stream, double* rho, double* u);

@@ -54,49 +54,46 @@ __global__ void macros_kernel(DevView v) {
     v.uy[i] = my / rho;
 }
 
-// FP64 [9][np] staging <-> state.
-template <typename T, typename S, bool DEV>
-__global__ void get_f_kernel(DevView v) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= v.n_cell) return;
-    T f[FVLBM_Q];
-    CellIO<S>::template load<T, DEV>(v.fa, i, v.inst[v.grp[i]], f);
-    for (int a = 0; a < FVLBM_Q; a++) v.conv[a * v.np + i] = DEV ? (double)f[a] + wgt<double>(a) : (double)f[a];
-}
+// f and rho, u in the caller's cell order, [n_cell][9] (get / set) or
+// [n_cell] and [n_cell][2] (macros), in a buffer the device reaches: the
+// caller's host buffer itself when the GPU reads pageable host memory, else
+// the device staging buffer v.conv that one copy moves to or from the host.
+// One thread per caller cell c.  get /
+// set pass a block's DIRECT_CELLS x 9 doubles through shared memory, so that
+// every warp access to the caller's buffer covers 32 consecutive doubles (a
+// per-thread row of 9 would touch each host line once per direction).
+constexpr int DIRECT_CELLS = 256;
 
 template <typename T, typename S, bool DEV>
-__global__ void set_f_kernel(DevView v) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= v.n_cell) return;
-    T f[FVLBM_Q];
-    for (int a = 0; a < FVLBM_Q; a++) {
-        const double x = v.conv[a * v.np + i];
-        f[a] = (T)(DEV ? x - wgt<double>(a) : x);
+__global__ void __launch_bounds__(DIRECT_CELLS) get_f_direct_kernel(DevView v, double* __restrict__ out) {
+    __shared__ double buf[DIRECT_CELLS * FVLBM_Q];
+    const int64_t c0 = (int64_t)blockIdx.x * DIRECT_CELLS;
+    const int64_t c = c0 + threadIdx.x;
+    if (c < v.n_cell) {
+        const int64_t i = v.iperm[c];
+        T f[FVLBM_Q];
+        CellIO<S>::template load<T, DEV>(v.fa, i, v.inst[v.grp[i]], f);
+        for (int a = 0; a < FVLBM_Q; a++)
+            buf[threadIdx.x * FVLBM_Q + a] = DEV ? (double)f[a] + wgt<double>(a) : (double)f[a];
     }
-    CellIO<S>::template store<T, DEV>(v.fa, i, v.inst[v.grp[i]], f);
-}
-
-// Direct access to a caller's buffer in caller order [n_cell][9] (get / set)
-// or [n_cell] and [n_cell][2] (macros): one thread per caller cell c, so that
-// the caller's buffer is read and written contiguously.
-template <typename T, typename S, bool DEV>
-__global__ void get_f_direct_kernel(DevView v, double* __restrict__ out) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= v.n_cell) return;
-    const int64_t i = v.iperm[c];
-    T f[FVLBM_Q];
-    CellIO<S>::template load<T, DEV>(v.fa, i, v.inst[v.grp[i]], f);
-    for (int a = 0; a < FVLBM_Q; a++) out[c * FVLBM_Q + a] = DEV ? (double)f[a] + wgt<double>(a) : (double)f[a];
+    __syncthreads();
+    const int nw = (int)(v.n_cell - c0 < DIRECT_CELLS ? v.n_cell - c0 : DIRECT_CELLS) * FVLBM_Q;
+    for (int w = threadIdx.x; w < nw; w += DIRECT_CELLS) out[c0 * FVLBM_Q + w] = buf[w];
 }
 
 template <typename T, typename S, bool DEV>
-__global__ void set_f_direct_kernel(DevView v, const double* __restrict__ in) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(DIRECT_CELLS) set_f_direct_kernel(DevView v, const double* __restrict__ in) {
+    __shared__ double buf[DIRECT_CELLS * FVLBM_Q];
+    const int64_t c0 = (int64_t)blockIdx.x * DIRECT_CELLS;
+    const int nw = (int)(v.n_cell - c0 < DIRECT_CELLS ? v.n_cell - c0 : DIRECT_CELLS) * FVLBM_Q;
+    for (int w = threadIdx.x; w < nw; w += DIRECT_CELLS) buf[w] = in[c0 * FVLBM_Q + w];
+    __syncthreads();
+    const int64_t c = c0 + threadIdx.x;
     if (c >= v.n_cell) return;
     const int64_t i = v.iperm[c];
     T f[FVLBM_Q];
     for (int a = 0; a < FVLBM_Q; a++) {
-        const double x = in[c * FVLBM_Q + a];
+        const double x = buf[threadIdx.x * FVLBM_Q + a];
         f[a] = (T)(DEV ? x - wgt<double>(a) : x);
     }
     CellIO<S>::template store<T, DEV>(v.fa, i, v.inst[v.grp[i]], f);
@@ -194,18 +191,6 @@ int launch_macros(const DevView& v, int prec, void* stream) {
                   return check_launch("macros kernel"));
 }
 
-int launch_get_f(const DevView& v, int prec, void* stream) {
-    cudaStream_t st = (cudaStream_t)stream;
-    DISPATCH_PREC(prec, get_f_kernel<T, S, DEV><<<grid_of(v.n_cell, 256), 256, 0, st>>>(v);
-                  return check_launch("get_f kernel"));
-}
-
-int launch_set_f(const DevView& v, int prec, void* stream) {
-    cudaStream_t st = (cudaStream_t)stream;
-    DISPATCH_PREC(prec, set_f_kernel<T, S, DEV><<<grid_of(v.n_cell, 256), 256, 0, st>>>(v);
-                  return check_launch("set_f kernel"));
-}
-
 int launch_reduce(const DevView& v, void* stream, int what) {
     cudaStream_t st = (cudaStream_t)stream;
     if (v.n_chunk > 0) reduce_chunks_kernel<<<(unsigned)v.n_chunk, RED_THREADS, 0, st>>>(v, what);
@@ -277,13 +262,13 @@ extern "C" int fvlbm_fma_peak(int32_t device, int32_t fp64, double* tflops) {
 namespace fvlbm {
 int launch_get_f_direct(const DevView& v, int prec, void* stream, double* f) {
     cudaStream_t st = (cudaStream_t)stream;
-    DISPATCH_PREC(prec, get_f_direct_kernel<T, S, DEV><<<grid_of(v.n_cell, 256), 256, 0, st>>>(v, f);
+    DISPATCH_PREC(prec, get_f_direct_kernel<T, S, DEV><<<grid_of(v.n_cell, DIRECT_CELLS), DIRECT_CELLS, 0, st>>>(v, f);
                   return check_launch("get_f kernel"));
 }
 
 int launch_set_f_direct(const DevView& v, int prec, void* stream, const double* f) {
     cudaStream_t st = (cudaStream_t)stream;
-    DISPATCH_PREC(prec, set_f_direct_kernel<T, S, DEV><<<grid_of(v.n_cell, 256), 256, 0, st>>>(v, f);
+    DISPATCH_PREC(prec, set_f_direct_kernel<T, S, DEV><<<grid_of(v.n_cell, DIRECT_CELLS), DIRECT_CELLS, 0, st>>>(v, f);
                   return check_launch("set_f kernel"));
 }
 

@@ -28,7 +28,6 @@ struct fvlbm_solver {
     int scheme = FVLBM_EULER;
     int64_t n_cell = 0;
     int32_t n_inst = 1;
-    std::vector<int64_t> perm;       // internal -> caller
     std::vector<int64_t> inst_begin;
     void* ws = nullptr;
     size_t ws_bytes = 0;
@@ -39,7 +38,6 @@ struct fvlbm_solver {
     // the device reads / writes the caller's host buffers directly (see fvlbm_host_transfer)
     bool host_can_direct = false;
     bool host_direct = false;
-    std::vector<double> h_conv, h_rho, h_ux, h_uy;
     // single-stage schemes on the fused stage alternate the state between
     // buf[0] and buf[1] (a tile must not overwrite cells other tiles still
     // read); v.fa is always the current state, buf[cur]
@@ -525,7 +523,6 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
     s->scheme = p0.scheme;
     s->n_cell = M.n_cell;
     s->n_inst = M.n_inst;
-    s->perm = M.perm;
     s->inst_begin = M.inst_begin;
     int pageable = 0;
     if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, p0.device) != cudaSuccess) {
@@ -696,14 +693,6 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
     CK(cudaMemcpyAsync(v.uold, v.ux, 8 * L.np, cudaMemcpyDeviceToDevice, s->stream), "snapshot u");
     CK(cudaMemcpyAsync(v.uold + L.np, v.uy, 8 * L.np, cudaMemcpyDeviceToDevice, s->stream), "snapshot v");
     CK(cudaStreamSynchronize(s->stream), "fvlbm_init");
-    try {
-        s->h_conv.resize((size_t)L.np * FVLBM_Q);
-        s->h_rho.resize(L.np);
-        s->h_ux.resize(L.np);
-        s->h_uy.resize(L.np);
-    } catch (const std::bad_alloc&) {
-        return fail(FVLBM_ERR_OOM, "fvlbm_init: out of host memory");
-    }
     return FVLBM_OK;
 }
 
@@ -936,23 +925,15 @@ extern "C" int fvlbm_macros(fvlbm_solver* s, double* rho, double* u) {
         int rc = launch_macros_direct(s->v, s->prec, s->stream, rho, u);
         return rc ? rc : sync_and_check(s);
     }
-    int rc = launch_macros(s->v, s->prec, s->stream);
+    // staged: caller order in the device staging buffer, then one copy per output
+    double* d_rho = s->v.conv;
+    double* d_u = s->v.conv + s->n_cell;
+    int rc = launch_macros_direct(s->v, s->prec, s->stream, rho ? d_rho : nullptr, u ? d_u : nullptr);
     if (rc) return rc;
-    const size_t bytes = 8 * (size_t)s->n_cell;
-    CK(cudaMemcpyAsync(s->h_rho.data(), s->v.rho, bytes, cudaMemcpyDeviceToHost, s->stream), "read rho");
-    CK(cudaMemcpyAsync(s->h_ux.data(), s->v.ux, bytes, cudaMemcpyDeviceToHost, s->stream), "read ux");
-    CK(cudaMemcpyAsync(s->h_uy.data(), s->v.uy, bytes, cudaMemcpyDeviceToHost, s->stream), "read uy");
-    rc = sync_and_check(s);
-    if (rc) return rc;
-    for (int64_t i = 0; i < s->n_cell; i++) {
-        const int64_t c = s->perm[i];
-        if (rho) rho[c] = s->h_rho[i];
-        if (u) {
-            u[2 * c] = s->h_ux[i];
-            u[2 * c + 1] = s->h_uy[i];
-        }
-    }
-    return FVLBM_OK;
+    // cudaMemcpyDefault: the caller's buffer may be host (pageable or pinned) or device memory
+    if (rho) CK(cudaMemcpyAsync(rho, d_rho, 8 * (size_t)s->n_cell, cudaMemcpyDefault, s->stream), "read rho");
+    if (u) CK(cudaMemcpyAsync(u, d_u, 16 * (size_t)s->n_cell, cudaMemcpyDefault, s->stream), "read u");
+    return sync_and_check(s);
 }
 
 static int reduce(fvlbm_solver* s, int what, std::vector<double>& out) {
@@ -998,17 +979,11 @@ extern "C" int fvlbm_get_f(fvlbm_solver* s, double* f) {
         int rc = launch_get_f_direct(s->v, s->prec, s->stream, f);
         return rc ? rc : sync_and_check(s);
     }
-    int rc = launch_get_f(s->v, s->prec, s->stream);
+    // staged: caller order in the device staging buffer, then one copy
+    int rc = launch_get_f_direct(s->v, s->prec, s->stream, s->v.conv);
     if (rc) return rc;
-    CK(cudaMemcpyAsync(s->h_conv.data(), s->v.conv, 8 * (size_t)s->v.np * FVLBM_Q, cudaMemcpyDeviceToHost, s->stream),
-       "read f");
-    rc = sync_and_check(s);
-    if (rc) return rc;
-    for (int64_t i = 0; i < s->n_cell; i++) {
-        const int64_t c = s->perm[i];
-        for (int a = 0; a < FVLBM_Q; a++) f[c * FVLBM_Q + a] = s->h_conv[(size_t)a * s->v.np + i];
-    }
-    return FVLBM_OK;
+    CK(cudaMemcpyAsync(f, s->v.conv, 8 * (size_t)s->n_cell * FVLBM_Q, cudaMemcpyDefault, s->stream), "read f");
+    return sync_and_check(s);
 }
 
 extern "C" int fvlbm_set_f(fvlbm_solver* s, const double* f) {
@@ -1020,14 +995,9 @@ extern "C" int fvlbm_set_f(fvlbm_solver* s, const double* f) {
     if (s->host_direct) {
         rc = launch_set_f_direct(s->v, s->prec, s->stream, f);
     } else {
-        for (int64_t i = 0; i < s->n_cell; i++) {
-            const int64_t c = s->perm[i];
-            for (int a = 0; a < FVLBM_Q; a++) s->h_conv[(size_t)a * s->v.np + i] = f[c * FVLBM_Q + a];
-        }
-        CK(cudaMemcpyAsync(s->v.conv, s->h_conv.data(), 8 * (size_t)s->v.np * FVLBM_Q, cudaMemcpyHostToDevice,
-                           s->stream),
-           "write f");
-        rc = launch_set_f(s->v, s->prec, s->stream);
+        // staged: one copy of the caller's buffer into the device staging buffer
+        CK(cudaMemcpyAsync(s->v.conv, f, 8 * (size_t)s->n_cell * FVLBM_Q, cudaMemcpyDefault, s->stream), "write f");
+        rc = launch_set_f_direct(s->v, s->prec, s->stream, s->v.conv);
     }
     if (rc) return rc;
     s->ab2_started = false;

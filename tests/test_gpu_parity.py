@@ -381,10 +381,12 @@ def test_graph_replay_matches_direct_launches(fv, scheme, kernel):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
-def test_host_transfer_modes_agree(fv, orc, prec):
+@pytest.mark.parametrize("name", ["cylinder", "cavity_quad"])
+def test_host_transfer_modes_agree(fv, orc, prec, name):
     """get_f / set_f / macros through the caller's buffers read and written by
-    the device directly give bitwise the same arrays as the staged copies."""
-    m = MESHES["cylinder"]()
+    the device directly give bitwise the same arrays as the staged copies
+    (768 cells: whole 256-cell transfer blocks; 576: a ragged last block)."""
+    m = MESHES[name]()
     f0 = f_random(orc, m, seed=31)
     out = {}
     for mode in ("staged", "auto"):
@@ -393,9 +395,21 @@ def test_host_transfer_modes_agree(fv, orc, prec):
         s.set_f(f0)
         s.step(7)
         out[mode] = (s.get_f(), *s.macros())
+        # a NULL output is skipped; the other is the same as with both requested
+        rho1, u1 = np.zeros(s.n_cell), np.zeros((s.n_cell, 2))
+        fv._check(fv.lib.fvlbm_macros(s._h, fv._d(rho1), None))
+        fv._check(fv.lib.fvlbm_macros(s._h, None, fv._d(u1)))
+        np.testing.assert_array_equal(rho1, out[mode][1])
+        np.testing.assert_array_equal(u1, out[mode][2])
         if prec != "fp16":   # the split format re-derives rho, u from the values it is given
-            # writing back the state read reproduces it exactly
+            # writing back the state read reproduces it exactly, from pageable
+            # and from pinned host memory
             s.set_f(out[mode][0])
+            assert np.array_equal(s.get_f(), out[mode][0])
+            import torch
+            pinned = torch.empty(out[mode][0].shape, dtype=torch.float64, pin_memory=True).numpy()
+            pinned[...] = out[mode][0]
+            s.set_f(pinned)
             assert np.array_equal(s.get_f(), out[mode][0])
         s.close()
     assert out["staged_direct"] is False
