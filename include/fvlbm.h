@@ -255,21 +255,23 @@ int fvlbm_get_f(fvlbm_solver* s, double* f);
 int fvlbm_set_f(fvlbm_solver* s, const double* f);
 
 /*
- * How fvlbm_get_f, fvlbm_set_f and fvlbm_macros move data between the
- * caller's host buffers and the device.
+ * How fvlbm_set_f reads the caller's buffer.
  *   FVLBM_HOST_AUTO (the default): when the device reports coherent access to
  *     pageable host memory (cudaDevAttrPageableMemoryAccess; GB300 reaches its
- *     Grace host's memory over NVLink-C2C), the kernels read and write the
- *     caller's buffer directly, in the caller's cell order: no host-side
- *     reordering, no staging copy.  Otherwise as FVLBM_HOST_STAGED.
- *   FVLBM_HOST_STAGED: one copy between the caller's buffer and a device
- *     staging buffer in the workspace (caller order); the kernels reorder on
- *     the device.
- * The buffers passed to those calls must be ordinary host memory (malloc,
- * numpy, pinned) or device memory; the calls synchronise before returning, so
- * the caller may reuse them at once.  The results are bitwise the same in both
- * modes.  direct: host, optional, written: 1 when the kernels access the
- * caller's buffers directly.  Errors: FVLBM_ERR_ARG.
+ *     Grace host's memory over NVLink-C2C), the kernel reads the caller's
+ *     buffer directly, in the caller's cell order, with no staging copy.
+ *     Otherwise as FVLBM_HOST_STAGED.
+ *   FVLBM_HOST_STAGED: one copy of the caller's buffer into a device staging
+ *     buffer in the workspace; the kernel reorders on the device.
+ * fvlbm_get_f and fvlbm_macros always write through that staging buffer and
+ * one copy: a device write into host pages the process has not touched yet
+ * faults each page in over the interconnect (measured ~50x slower into a
+ * fresh 480 MB array), and into touched pages the copy is as fast.
+ * The buffers passed to those calls may be host memory (malloc, numpy, pinned)
+ * or device memory; the calls synchronise before returning, so the caller may
+ * reuse them at once.  The results are bitwise the same in both modes.
+ * direct: host, optional, written: 1 when fvlbm_set_f reads the caller's
+ * buffer directly.  Errors: FVLBM_ERR_ARG.
  */
 typedef enum fvlbm_host_mode { FVLBM_HOST_AUTO = 0, FVLBM_HOST_STAGED = 1 } fvlbm_host_mode;
 int fvlbm_host_transfer(fvlbm_solver* s, int32_t mode, int32_t* direct);

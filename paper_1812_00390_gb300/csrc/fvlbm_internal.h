@@ -171,9 +171,9 @@ int launch_macros(const DevView& v, int prec, void* stream);
 int launch_reduce(const DevView& v, void* stream, int what);
 // f and the macros in the caller's cell order, in a buffer the device
 // accesses (host memory reachable by the GPU, or device memory).
-int launch_get_f_direct(const DevView& v, int prec, void* stream, double* f);
-int launch_set_f_direct(const DevView& v, int prec, void* stream, const double* f);
-int launch_macros_direct(const DevView& v, int prec, void* stream, double* rho, double* u);
+int launch_get_f_ordered(const DevView& v, int prec, void* stream, double* f);
+int launch_set_f_ordered(const DevView& v, int prec, void* stream, const double* f);
+int launch_macros_ordered(const DevView& v, int prec, void* stream, double* rho, double* u);
 
 // Solver internals for entry points defined outside the solver's own file.
 struct SolverRef {

@@ -55,19 +55,19 @@ __global__ void macros_kernel(DevView v) {
 }
 
 // f and rho, u in the caller's cell order, [n_cell][9] (get / set) or
-// [n_cell] and [n_cell][2] (macros), in a buffer the device reaches: the
-// caller's host buffer itself when the GPU reads pageable host memory, else
-// the device staging buffer v.conv that one copy moves to or from the host.
-// One thread per caller cell c.  get /
-// set pass a block's DIRECT_CELLS x 9 doubles through shared memory, so that
-// every warp access to the caller's buffer covers 32 consecutive doubles (a
-// per-thread row of 9 would touch each host line once per direction).
-constexpr int DIRECT_CELLS = 256;
+// [n_cell] and [n_cell][2] (macros), in a buffer the device reaches: for set
+// the caller's host buffer itself when the GPU reads pageable host memory,
+// otherwise (and for get and macros) the device staging buffer v.conv that one
+// copy fills or empties.  One thread per caller cell c.  get / set pass a
+// block's ORDERED_CELLS x 9 doubles through shared memory, so that every warp
+// access to the caller's buffer covers 32 consecutive doubles (a per-thread
+// row of 9 would touch each host line once per direction).
+constexpr int ORDERED_CELLS = 256;
 
 template <typename T, typename S, bool DEV>
-__global__ void __launch_bounds__(DIRECT_CELLS) get_f_direct_kernel(DevView v, double* __restrict__ out) {
-    __shared__ double buf[DIRECT_CELLS * FVLBM_Q];
-    const int64_t c0 = (int64_t)blockIdx.x * DIRECT_CELLS;
+__global__ void __launch_bounds__(ORDERED_CELLS) get_f_ordered_kernel(DevView v, double* __restrict__ out) {
+    __shared__ double buf[ORDERED_CELLS * FVLBM_Q];
+    const int64_t c0 = (int64_t)blockIdx.x * ORDERED_CELLS;
     const int64_t c = c0 + threadIdx.x;
     if (c < v.n_cell) {
         const int64_t i = v.iperm[c];
@@ -77,16 +77,16 @@ __global__ void __launch_bounds__(DIRECT_CELLS) get_f_direct_kernel(DevView v, d
             buf[threadIdx.x * FVLBM_Q + a] = DEV ? (double)f[a] + wgt<double>(a) : (double)f[a];
     }
     __syncthreads();
-    const int nw = (int)(v.n_cell - c0 < DIRECT_CELLS ? v.n_cell - c0 : DIRECT_CELLS) * FVLBM_Q;
-    for (int w = threadIdx.x; w < nw; w += DIRECT_CELLS) out[c0 * FVLBM_Q + w] = buf[w];
+    const int nw = (int)(v.n_cell - c0 < ORDERED_CELLS ? v.n_cell - c0 : ORDERED_CELLS) * FVLBM_Q;
+    for (int w = threadIdx.x; w < nw; w += ORDERED_CELLS) out[c0 * FVLBM_Q + w] = buf[w];
 }
 
 template <typename T, typename S, bool DEV>
-__global__ void __launch_bounds__(DIRECT_CELLS) set_f_direct_kernel(DevView v, const double* __restrict__ in) {
-    __shared__ double buf[DIRECT_CELLS * FVLBM_Q];
-    const int64_t c0 = (int64_t)blockIdx.x * DIRECT_CELLS;
-    const int nw = (int)(v.n_cell - c0 < DIRECT_CELLS ? v.n_cell - c0 : DIRECT_CELLS) * FVLBM_Q;
-    for (int w = threadIdx.x; w < nw; w += DIRECT_CELLS) buf[w] = in[c0 * FVLBM_Q + w];
+__global__ void __launch_bounds__(ORDERED_CELLS) set_f_ordered_kernel(DevView v, const double* __restrict__ in) {
+    __shared__ double buf[ORDERED_CELLS * FVLBM_Q];
+    const int64_t c0 = (int64_t)blockIdx.x * ORDERED_CELLS;
+    const int nw = (int)(v.n_cell - c0 < ORDERED_CELLS ? v.n_cell - c0 : ORDERED_CELLS) * FVLBM_Q;
+    for (int w = threadIdx.x; w < nw; w += ORDERED_CELLS) buf[w] = in[c0 * FVLBM_Q + w];
     __syncthreads();
     const int64_t c = c0 + threadIdx.x;
     if (c >= v.n_cell) return;
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(DIRECT_CELLS) set_f_direct_kernel(DevView v, c
 }
 
 template <typename T, typename S, bool DEV>
-__global__ void macros_direct_kernel(DevView v, double* __restrict__ rho_out, double* __restrict__ u_out) {
+__global__ void macros_ordered_kernel(DevView v, double* __restrict__ rho_out, double* __restrict__ u_out) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= v.n_cell) return;
     const int64_t i = v.iperm[c];
@@ -260,21 +260,21 @@ extern "C" int fvlbm_fma_peak(int32_t device, int32_t fp64, double* tflops) {
 }
 
 namespace fvlbm {
-int launch_get_f_direct(const DevView& v, int prec, void* stream, double* f) {
+int launch_get_f_ordered(const DevView& v, int prec, void* stream, double* f) {
     cudaStream_t st = (cudaStream_t)stream;
-    DISPATCH_PREC(prec, get_f_direct_kernel<T, S, DEV><<<grid_of(v.n_cell, DIRECT_CELLS), DIRECT_CELLS, 0, st>>>(v, f);
+    DISPATCH_PREC(prec, get_f_ordered_kernel<T, S, DEV><<<grid_of(v.n_cell, ORDERED_CELLS), ORDERED_CELLS, 0, st>>>(v, f);
                   return check_launch("get_f kernel"));
 }
 
-int launch_set_f_direct(const DevView& v, int prec, void* stream, const double* f) {
+int launch_set_f_ordered(const DevView& v, int prec, void* stream, const double* f) {
     cudaStream_t st = (cudaStream_t)stream;
-    DISPATCH_PREC(prec, set_f_direct_kernel<T, S, DEV><<<grid_of(v.n_cell, DIRECT_CELLS), DIRECT_CELLS, 0, st>>>(v, f);
+    DISPATCH_PREC(prec, set_f_ordered_kernel<T, S, DEV><<<grid_of(v.n_cell, ORDERED_CELLS), ORDERED_CELLS, 0, st>>>(v, f);
                   return check_launch("set_f kernel"));
 }
 
-int launch_macros_direct(const DevView& v, int prec, void* stream, double* rho, double* u) {
+int launch_macros_ordered(const DevView& v, int prec, void* stream, double* rho, double* u) {
     cudaStream_t st = (cudaStream_t)stream;
-    DISPATCH_PREC(prec, macros_direct_kernel<T, S, DEV><<<grid_of(v.n_cell, 256), 256, 0, st>>>(v, rho, u);
+    DISPATCH_PREC(prec, macros_ordered_kernel<T, S, DEV><<<grid_of(v.n_cell, 256), 256, 0, st>>>(v, rho, u);
                   return check_launch("macros kernel"));
 }
 }  // namespace fvlbm

@@ -35,7 +35,7 @@ struct fvlbm_solver {
     DevView v{};
     std::vector<InstParam> inst;
     bool ab2_started = false;
-    // the device reads / writes the caller's host buffers directly (see fvlbm_host_transfer)
+    // set_f reads the caller's host buffer directly (see fvlbm_host_transfer)
     bool host_can_direct = false;
     bool host_direct = false;
     // single-stage schemes on the fused stage alternate the state between
@@ -921,14 +921,11 @@ extern "C" int fvlbm_macros(fvlbm_solver* s, double* rho, double* u) {
     clear_error();
     if (!s) return fail(FVLBM_ERR_ARG, "fvlbm_macros: null solver");
     DeviceGuard dg(s->device);
-    if (s->host_direct) {
-        int rc = launch_macros_direct(s->v, s->prec, s->stream, rho, u);
-        return rc ? rc : sync_and_check(s);
-    }
-    // staged: caller order in the device staging buffer, then one copy per output
+    // caller order in the device staging buffer, then one copy per output
+    // (device -> host always staged; see fvlbm_host_transfer)
     double* d_rho = s->v.conv;
     double* d_u = s->v.conv + s->n_cell;
-    int rc = launch_macros_direct(s->v, s->prec, s->stream, rho ? d_rho : nullptr, u ? d_u : nullptr);
+    int rc = launch_macros_ordered(s->v, s->prec, s->stream, rho ? d_rho : nullptr, u ? d_u : nullptr);
     if (rc) return rc;
     // cudaMemcpyDefault: the caller's buffer may be host (pageable or pinned) or device memory
     if (rho) CK(cudaMemcpyAsync(rho, d_rho, 8 * (size_t)s->n_cell, cudaMemcpyDefault, s->stream), "read rho");
@@ -975,12 +972,9 @@ extern "C" int fvlbm_get_f(fvlbm_solver* s, double* f) {
     clear_error();
     if (!s || !f) return fail(FVLBM_ERR_ARG, "fvlbm_get_f: null argument");
     DeviceGuard dg(s->device);
-    if (s->host_direct) {
-        int rc = launch_get_f_direct(s->v, s->prec, s->stream, f);
-        return rc ? rc : sync_and_check(s);
-    }
-    // staged: caller order in the device staging buffer, then one copy
-    int rc = launch_get_f_direct(s->v, s->prec, s->stream, s->v.conv);
+    // caller order in the device staging buffer, then one copy (device -> host
+    // always staged; see fvlbm_host_transfer)
+    int rc = launch_get_f_ordered(s->v, s->prec, s->stream, s->v.conv);
     if (rc) return rc;
     CK(cudaMemcpyAsync(f, s->v.conv, 8 * (size_t)s->n_cell * FVLBM_Q, cudaMemcpyDefault, s->stream), "read f");
     return sync_and_check(s);
@@ -993,11 +987,11 @@ extern "C" int fvlbm_set_f(fvlbm_solver* s, const double* f) {
     CK(cudaStreamSynchronize(s->stream), "synchronise");
     int rc;
     if (s->host_direct) {
-        rc = launch_set_f_direct(s->v, s->prec, s->stream, f);
+        rc = launch_set_f_ordered(s->v, s->prec, s->stream, f);
     } else {
         // staged: one copy of the caller's buffer into the device staging buffer
         CK(cudaMemcpyAsync(s->v.conv, f, 8 * (size_t)s->n_cell * FVLBM_Q, cudaMemcpyDefault, s->stream), "write f");
-        rc = launch_set_f_direct(s->v, s->prec, s->stream, s->v.conv);
+        rc = launch_set_f_ordered(s->v, s->prec, s->stream, s->v.conv);
     }
     if (rc) return rc;
     s->ab2_started = false;

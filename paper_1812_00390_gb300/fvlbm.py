@@ -304,9 +304,10 @@ class Solver:
         return k.value
 
     def host_transfer(self, mode: str = "auto") -> bool:
-        """How get_f / set_f / macros reach host buffers: "auto" (direct device
-        access when the GPU can reach pageable host memory) or "staged".
-        Returns True when the direct path is in use."""
+        """How set_f reads the caller's buffer: "auto" (the kernel reads it
+        directly when the GPU can reach pageable host memory) or "staged" (one
+        copy to a device buffer).  get_f and macros always copy through the
+        device buffer.  Returns True when set_f reads directly."""
         d = C.c_int32()
         _check(lib.fvlbm_host_transfer(self._h, {"auto": 0, "staged": 1}[mode], C.byref(d)))
         return bool(d.value)

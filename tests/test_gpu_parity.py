@@ -383,8 +383,8 @@ def test_graph_replay_matches_direct_launches(fv, scheme, kernel):
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
 @pytest.mark.parametrize("name", ["cylinder", "cavity_quad"])
 def test_host_transfer_modes_agree(fv, orc, prec, name):
-    """get_f / set_f / macros through the caller's buffers read and written by
-    the device directly give bitwise the same arrays as the staged copies
+    """set_f reading the caller's buffer directly and set_f through the device
+    staging copy give bitwise the same state; get_f / macros read it back
     (768 cells: whole 256-cell transfer blocks; 576: a ragged last block)."""
     m = MESHES[name]()
     f0 = f_random(orc, m, seed=31)
