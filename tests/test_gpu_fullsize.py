@@ -34,7 +34,9 @@ def _offsets(variants, inst):
     return off
 
 
-@pytest.mark.parametrize("prec,kernel,tol", [("fp32", 512, 2e-6), ("fp64", 1, 1e-12)])
+# measured maxima over the picks after 20 steps: FP32 1.1e-6, FP64 1.7e-14,
+# FP16 split 4.7e-4 (low-Re cavities; the non-equilibrium part is stored in 16 bits)
+@pytest.mark.parametrize("prec,kernel,tol", [("fp32", 512, 2e-6), ("fp64", 1, 1e-12), ("fp16", 512, 2e-3)])
 def test_full_batch_sampled_instances_match_oracle(fv, orc, batch, prec, kernel, tol):
     bench, variants, inst = batch
     s, handles = bench.build_solver(fv, variants, inst, prec, kernel=kernel)
@@ -57,6 +59,7 @@ def test_full_batch_sampled_instances_match_oracle(fv, orc, batch, prec, kernel,
         sl = slice(off[k], off[k + 1])
         err_u = np.abs(u_all[sl] - u_o).max() / np.abs(u_o).max()
         err_r = np.abs(rho_all[sl] - rho_o).max()
+        print(prec, k, key[0], "rel |u| error", err_u, "rho error", err_r)
         assert err_u < tol and err_r < tol, (k, key, err_u, err_r)
     # properties at full size: every instance finite, closed instances conserve mass
     assert np.isfinite(u_all).all() and np.isfinite(rho_all).all()
