@@ -166,11 +166,17 @@ def test_fused_single_stage_many_tiles(fv, scheme):
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 @pytest.mark.parametrize("scheme", ["euler", "ab2", "rk4"])
-def test_fused_stage_16bit_formats(fv, orc, prec, scheme):
+@pytest.mark.parametrize("name", ["cylinder", "bricks"])
+def test_fused_stage_16bit_formats(fv, orc, prec, scheme, name):
     """The 16-bit split formats through the fused stage (raw staging and decode
     in shared memory; alternating state for Euler / AB2) agree with the
-    two-kernel stage, which decodes the same storage from global memory."""
-    m = MESHES["cylinder"]()
+    two-kernel stage, which decodes the same storage from global memory
+    (triangles and quads: 4 slots per cell; polygons: 8).  The two kernels
+    round differently in FP32, which can move a stored 16-bit non-equilibrium
+    component by one 16-bit step (2^-10 of it in FP16, 2^-7 in BF16); with
+    |n| up to ~1e-2 of f here that allows ~1e-5 (FP16) / ~1e-4 (BF16) per
+    flip, hence the bounds, an order above."""
+    m = MESHES[name]()
     tau = 0.15
     dt = orc.Oracle(m).cfl_dt(0.5, 0.1, tau, scheme)
     f0 = f_random(orc, m, seed=29, noise=0.01)
@@ -182,7 +188,9 @@ def test_fused_stage_16bit_formats(fv, orc, prec, scheme):
             s.step(n)
         out.append(s.get_f())
         s.close()
-    assert rel_err(out[1], out[0]) < 1e-5
+    err = rel_err(out[1], out[0])
+    print(name, prec, scheme, "fused vs two-kernel", err)
+    assert err < {"fp16": 1e-4, "bf16": 1e-3}[prec], err
 
 
 def test_fused_tiles_span_instances(fv):
