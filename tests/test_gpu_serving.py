@@ -102,3 +102,34 @@ def test_poisson_driver_small(fv):
     assert s["requests"] == 6 and s["p99_s"] >= s["p50_s"] > 0 and s["aggregate_mcups"] > 0
     assert all(x["state"] == fv.REQ_DONE for x in infos)
     srv.close()
+
+
+def test_request_converges_to_the_residual_tolerance(fv, orc):
+    """A request that really converges: the 16 x 4 Couette channel (walls at
+    y = 0 and H = 4, top wall at U = 0.1, periodic in x) run through the server
+    with the paper's residual check every 1000 steps (Sec. 3.2) stops at the
+    first check with e <= 1e-8, well before the step cap, at the linear steady
+    profile u = U y / H of Sec. 3.1 (O(h^2) on the jittered mesh), and its
+    state is the one a solo solver reaches in the same number of steps
+    (measured: stops at 7000 steps with e = 4.5e-9, profile error 7.1e-5)."""
+    m = mg.couette(16, 4)
+    h = fv.Mesh(m)
+    p = fv.make_params(0.24, scheme="euler", precision="fp64")
+    srv = fv.Server(1 << 28, check_interval=1000, residual_tol=1e-8, max_steps=100_000)
+    rid = srv.submit(h, p)
+    while srv.poll() == 0:
+        pass
+    info = srv.request(rid, fields=True)
+    srv.close()
+    assert info["state"] == fv.REQ_DONE
+    assert info["residual"] <= 1e-8 and info["steps"] % 1000 == 0 and info["steps"] < 100_000
+    _, c, _ = orc.Oracle(m).geometry()
+    err = np.abs(info["u"][:, 0] - 0.1 * c[:, 1] / 4.0).max()
+    print("Couette 16x4 through the server:", info["steps"], "steps, e =", info["residual"], "profile error", err)
+    assert err < 2e-4 and np.abs(info["u"][:, 1]).max() < 2e-4
+    s = fv.Solver(fv.Mesh(m), p)
+    s.step(info["steps"])
+    rho, u = s.macros()
+    s.close()
+    np.testing.assert_array_equal(u, info["u"])
+    np.testing.assert_array_equal(rho, info["rho"])
