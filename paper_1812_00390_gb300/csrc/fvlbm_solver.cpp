@@ -175,6 +175,13 @@ bool try_tile(const Mesh& M, int maxf, int64_t c0, int len, int threads, int ls,
         }
     const int n1 = (int)W.r1.size();
     if (nl > ls || len + n1 > threads) return false;
+    // 1-ring and 2-ring each in global order: the kernel gathers them with
+    // consecutive threads, which then share the rows of a 32-cell block
+    std::sort(W.r1.begin(), W.r1.end());
+    std::sort(W.r2.begin(), W.r2.end());
+    int x = len;
+    for (int64_t j : W.r1) W.loc[j] = x++;
+    for (int64_t q : W.r2) W.loc[q] = x++;
     W.t_nb.assign((size_t)len * maxf, -1);
     W.t_f.assign((size_t)len * maxf, -1);
     W.r_nb.assign((size_t)n1 * maxf, -1);
