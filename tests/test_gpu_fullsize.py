@@ -35,8 +35,10 @@ def _offsets(variants, inst):
 
 
 # measured maxima over the picks after 20 steps: FP32 1.1e-6, FP64 1.7e-14,
-# FP16 split 4.7e-4 (low-Re cavities; the non-equilibrium part is stored in 16 bits)
-@pytest.mark.parametrize("prec,kernel,tol", [("fp32", 512, 2e-6), ("fp64", 1, 1e-12), ("fp16", 512, 2e-3)])
+# FP16 split 4.7e-4, BF16 split 4.5e-3 (low-Re cavities; the non-equilibrium
+# part is stored in 16 bits: 11 significant bits in FP16, 8 in BF16)
+@pytest.mark.parametrize("prec,kernel,tol", [("fp32", 512, 2e-6), ("fp64", 1, 1e-12), ("fp16", 512, 2e-3),
+                                             ("bf16", 512, 2e-2)])
 def test_full_batch_sampled_instances_match_oracle(fv, orc, batch, prec, kernel, tol):
     bench, variants, inst = batch
     s, handles = bench.build_solver(fv, variants, inst, prec, kernel=kernel)
