@@ -281,24 +281,27 @@ def kernel_source_sha() -> str:
 
 
 def ncu_traffic(workload: str):
-    """DRAM bytes per cell and stage from the committed ncu summary of this
-    workload, or None when it is missing or was taken on other kernel source."""
-    p = os.path.join(ROOT, "profiles", f"stage_kernels_{workload}.md")
-    if not os.path.exists(p):
-        return None
-    txt = open(p).read()
-    m = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", txt)
-    t = re.search(r"dram_bytes_per_cell_stage:\s*([0-9.eE+-]+)", txt)
-    if not m or not t or m.group(1) != kernel_source_sha():
-        return None
-    return float(t.group(1))
+    """(DRAM bytes per cell and stage, where they come from) for the stage
+    kernel of this workload from profiles/ncu_traffic.json (written by hand
+    from an ncu capture, keyed by the kernel-source hash), or (None, reason)
+    when it is missing or was taken on other kernel source."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(p))[workload]
+    except (OSError, ValueError, KeyError):
+        return None, "no ncu capture recorded for this workload"
+    if d.get("kernel_source_sha") != kernel_source_sha():
+        return None, "the recorded ncu capture is of other kernel source"
+    return float(d["dram_bytes_per_cell_stage"]), d.get("capture", "")
 
 
 # ----------------------------------------------------------------------------- oracle baseline
-def oracle_mcups(variants, inst, budget_s: float, steps_cap: int = 100000):
-    """The FP64 oracle, as it stands, on one instance of each kind, RK2."""
+def oracle_mcups(variants, inst, budget_s: float, steps_cap: int = 100000, threads: int = 0):
+    """The FP64 oracle, as it stands, on one instance of each kind, RK2, with
+    `threads` OpenMP threads (0: all the host's cores)."""
     import oracle
     oracle.build()
+    used = oracle.threads(threads if threads > 0 else (os.cpu_count() or 1))
     picked = {}
     for key, tau, u0 in inst:
         picked.setdefault(key[0], (key, tau, u0))
@@ -317,10 +320,9 @@ def oracle_mcups(variants, inst, budget_s: float, steps_cap: int = 100000):
             o.run("rk2", tau, dt, 1)
         steps += 1
     el = time.perf_counter() - t0
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     sample = (f"{len(runs)} instances ({'+'.join(k for k in picked)}, {cells} cells), "
-              f"{steps} RK2 steps each, {el:.1f} s")
-    return cells * steps / el / 1e6, threads, sample, el, steps, cells
+              f"{steps} RK2 steps each, {el:.1f} s, {used} thread{'s' if used > 1 else ''}")
+    return cells * steps / el / 1e6, used, sample, el, steps, cells
 
 
 # ----------------------------------------------------------------------------- arms
@@ -386,7 +388,9 @@ def run_ours(args):
     cpu = None
     if rank == 0 and not args.no_cpu:
         v, thr, sample, _, _, _ = oracle_mcups(variants, inst, args.cpu_seconds)
-        cpu = {"value": v, "unit": "MCUPS", "cores": thr, "kind": "oracle", "sample": sample}
+        v1, _, sample1, _, _, _ = oracle_mcups(variants, inst, args.cpu_seconds / 2, threads=1)
+        cpu = {"value": v, "unit": "MCUPS", "cores": thr, "kind": "oracle", "sample": sample,
+               "single_thread": {"value": v1, "unit": "MCUPS", "cores": 1, "sample": sample1}}
 
     handles = {k: fv.Mesh(m) for k, m in variants.items()}
     # the batch runs the library's automatic choice (or --kernel); the
@@ -478,10 +482,13 @@ def run_ours(args):
     stage_ms = float(sum(kern_ms))
     achieved = alg_per_cell_stage * n_cells / (stage_ms / 1e3) / 1e9
     peak, peak_src = measured_peaks()
-    traffic_pc = ncu_traffic(args.workload)
+    traffic_pc, traffic_src = ncu_traffic(args.workload)
     names = ["stage_tile_kernel"] if len(kern_ms) == 1 else ["face_values_kernel", "update_kernel"]
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": (traffic_pc * n_cells if traffic_pc else None),
+            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per cell and stage, "
+                               "profiles/ncu_traffic.json (%s), scaled to this launch's cells" % traffic_src
+                               if traffic_pc else traffic_src),
             "kernel": ("stage_tile_kernel (one fused RK2 stage)" if len(kern_ms) == 1
                        else "one RK2 stage = face_values_kernel + update_kernel"),
             "kernel_ms": {n: float(t) for n, t in zip(names, kern_ms)},
@@ -499,29 +506,36 @@ def run_ours(args):
             else f"{peak_src} {HBM_FALLBACK_GBS:.0f} GB/s"}
 
     # end to end through the C ABI with host buffers: each e2e step uploads the
-    # state from host memory, advances e2e_inner time steps, reads back the
-    # per-instance residual.  The headline uses a pinned host buffer; the same
-    # loop from the pageable array get_f returns is reported beside it.
+    # state from host memory (set_f), advances e2e_inner time steps and reads
+    # the solution back (macros: rho and u of every cell into host arrays).
+    # The headline uses pinned host buffers; the same loop with pageable numpy
+    # arrays is reported beside it.
     e2e_inner = args.e2e_inner
     e2e_val = e2e_pageable = None
     if args.e2e_steps > 0:
         f_host = s32.get_f()
         f_pinned = torch.empty(f_host.shape, dtype=torch.float64, pin_memory=True).numpy()
         f_pinned[...] = f_host
+        rho_pinned = torch.empty(n_cells, dtype=torch.float64, pin_memory=True).numpy()
+        u_pinned = torch.empty((n_cells, 2), dtype=torch.float64, pin_memory=True).numpy()
+        rho_page, u_page = np.zeros(n_cells), np.zeros((n_cells, 2))
 
-        def e2e_loop(buf):
+        def e2e_loop(buf, rho_out, u_out):
             s32.sync()
             barrier()
             t0 = time.perf_counter()
             for _ in range(args.e2e_steps):
                 s32.set_f(buf)
                 s32.step(e2e_inner)
-                s32.residual()
+                s32.macros_into(rho_out, u_out)
             torch.cuda.synchronize()
             return n_cells * world * e2e_inner * args.e2e_steps / (time.perf_counter() - t0) / 1e6
 
-        e2e_pageable = e2e_loop(f_host)
-        e2e_val = e2e_loop(f_pinned)
+        e2e_pageable = e2e_loop(f_host, rho_page, u_page)
+        e2e_val = e2e_loop(f_pinned, rho_pinned, u_pinned)
+        # the read-back is the solution: it equals what macros() returns
+        _, u_chk = s32.macros()
+        e2e_readback_ok = bool(np.array_equal(u_chk, u_pinned))
 
     configs = config_runs(fv, torch, dev) if (args.configs and rank == 0) else None
     roof_syn = roofline_synthetic(fv, torch, peak) if (args.configs and rank == 0) else None
@@ -566,9 +580,12 @@ def run_ours(args):
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": ({"value": e2e_val, "unit": "MCUPS", "h2d_bytes_per_step": n_cells * 9 * 8,
-                     "d2h_bytes_per_step": 8 * args.instances + 4,
-                     "definition": f"set_f from host + {e2e_inner} time steps + residual read-back",
-                     "host_memory": "pinned", "pageable_value": e2e_pageable}
+                     "d2h_bytes_per_step": n_cells * 3 * 8,
+                     "definition": (f"per e2e step: set_f of the whole state from host memory (FP64, "
+                                    f"caller order) + {e2e_inner} time steps + macros (rho, u of every cell "
+                                    f"into host arrays); the byte counts are per e2e step"),
+                     "host_memory": "pinned", "pageable_value": e2e_pageable,
+                     "readback_equals_macros": e2e_readback_ok}
                     if e2e_val is not None else None),
             "serving": serving,
             "single_configs": configs,

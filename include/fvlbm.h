@@ -237,14 +237,20 @@ int fvlbm_mass(fvlbm_solver* s, double* mass);
  *   s     solver (its state and geometry are the inputs)
  *   mass  host [n_instances], written
  * The block partial sums live in a fixed 96 KB array in the library's device
- * memory (allocated when the library loads, held by every GPU that loads it
- * until the process exits), not in the solver's workspace.  Limits: at most
- * 8192 chunks of 4096 cells (33,554,432 cells) and 4096 instances per solver;
- * larger solvers get FVLBM_ERR_ARG with the limits in the message.
- * The first call on a device looks up the array's device address; make that
- * first call before any stream capture.  Every call on a device shares the
- * array, so calls that overlap on the GPU (other threads, other streams)
- * race; serialise them.  Nothing carries over from an earlier call.
+ * memory, not in the solver's workspace.  The array is part of the library's
+ * device code: under CUDA's default lazy module loading that code, with the
+ * array, is loaded into a device's memory by the first call of this function
+ * on that device, which also looks up the array's device address.  The first
+ * call on each device may therefore allocate: make it once before the region
+ * in which the caller may not allocate, and before any stream capture (with
+ * CUDA_MODULE_LOADING=EAGER the array is loaded when the process first uses
+ * the device instead).  Every later call allocates nothing.  The array stays
+ * on every device it was loaded on until the process exits.
+ * Limits: at most 8192 chunks of 4096 cells (33,554,432 cells) and 4096
+ * instances per solver; larger solvers get FVLBM_ERR_ARG with the limits in
+ * the message.  Every call on a device shares the array, so calls that
+ * overlap on the GPU (other threads, other streams) race; serialise them.
+ * Nothing carries over from an earlier call.
  * Synchronises the solver's stream.  Errors: FVLBM_ERR_ARG, _CUDA, _DIVERGED.
  */
 int fvlbm_mass_noalloc(fvlbm_solver* s, double* mass);
@@ -387,6 +393,107 @@ int fvlbm_server_poll(fvlbm_server* s, int32_t* n_completed);
 int fvlbm_server_request(fvlbm_server* s, int64_t id, fvlbm_request_info* info, double* rho, double* u);
 int fvlbm_server_stats(const fvlbm_server* s, fvlbm_server_stats_t* stats);
 void fvlbm_server_destroy(fvlbm_server* s);
+
+/*
+ * Domain decomposition of one mesh (Sec. 3: the paper's solver runs in
+ * Code_Saturne's parallel modules; Conclusions, item 4: one ghost layer per
+ * partition interface).  The cells are split into parts by recursive
+ * coordinate bisection of their centroids.  A part updates its own cells and
+ * holds two rings of ghost cells: ring 1, the cells outside the part that share
+ * a face with one of its cells (their least-squares gradients, Eq.
+ * leastsquare, are recomputed by the part, since the upwind value on a shared
+ * face comes from them, Eq. lslrflux), and ring 2, the cells that share a face
+ * with ring 1 (their state only).  After every stage the owner of each ghost
+ * sends its new state: one halo exchange of two rings per stage.  Every
+ * cell's arithmetic is the same as in the undivided solve, so the result is
+ * bitwise the same.
+ *
+ * The plan (host only, no GPU needed):
+ */
+#define FVLBM_MAX_PARTS 64
+
+typedef struct fvlbm_partition fvlbm_partition;
+
+typedef struct fvlbm_part_info_s {
+    int64_t n_owned;      /* cells the part updates */
+    int64_t n_ring1;      /* ghost ring 1 */
+    int64_t n_ring2;      /* ghost ring 2 */
+    int64_t n_recv;       /* ghost cells received per stage (n_ring1 + n_ring2) */
+    int64_t n_send;       /* owned cells sent per stage, summed over the receiving parts */
+    int32_t n_neighbours; /* parts it receives from */
+} fvlbm_part_info_t;
+
+/*
+ * Partition a mesh of one instance into n_parts parts (1..FVLBM_MAX_PARTS, at
+ * most one per cell).  Cut: across the longer extent of the centroids'
+ * bounding box, at the cell count proportional to the parts on each side
+ * (ties broken by cell number): part sizes differ by at most one cell per
+ * level of bisection.  The plan copies what it keeps; the mesh may be
+ * destroyed afterwards.  Errors: FVLBM_ERR_ARG (several instances, n_parts out
+ * of range), _OOM.
+ */
+int fvlbm_mesh_partition(const fvlbm_mesh* mesh, int32_t n_parts, fvlbm_partition** out);
+void fvlbm_partition_destroy(fvlbm_partition* p);
+/* Sizes of part `part`.  info: host, written.  Errors: FVLBM_ERR_ARG. */
+int fvlbm_partition_info(const fvlbm_partition* p, int32_t part, fvlbm_part_info_t* info);
+/*
+ * The cells of part `part` in its local numbering: cells[l] is the caller's
+ * number (in the partitioned mesh) of local cell l; the owned cells come
+ * first in ascending order, then ring 1, then ring 2, each ascending.
+ * cells: host [n_owned + n_ring1 + n_ring2], written.  Errors: FVLBM_ERR_ARG.
+ */
+int fvlbm_partition_cells(const fvlbm_partition* p, int32_t part, int64_t* cells);
+/*
+ * The message part `src` sends part `dst` after every stage: *count entries;
+ * entry e is owned local cell src_local[e] of src, stored into ghost local
+ * cell dst_local[e] of dst (local numberings of fvlbm_partition_cells).  With
+ * src_local / dst_local NULL only *count is written (0 when src sends dst
+ * nothing).  Every ghost of every part appears in exactly one message, from
+ * the part that owns it.  count: host, written; src_local, dst_local: host
+ * [*count] or NULL.  Errors: FVLBM_ERR_ARG.
+ */
+int fvlbm_partition_halo(const fvlbm_partition* p, int32_t src, int32_t dst, int64_t* count, int32_t* src_local,
+                         int32_t* dst_local);
+
+/*
+ * A partitioned solve on one GPU: one solver per part (each with its own
+ * workspace, allocated by the library), all on one stream, with the halo
+ * exchange after every stage as a device-to-device copy of the ghost states
+ * (one kernel over all messages).  The FP64 reductions (mass, residual) sum
+ * the parts' FP64 partial sums in part order.  A multi-GPU run would place
+ * one part per GPU and carry the same messages over the interconnect; this
+ * library runs all parts on the device of params->device.
+ *   plan     partition (must stay valid until fvlbm_dd_destroy)
+ *   params   host, one set for the whole mesh (n_params = 1); params->kernel
+ *            is used by every part
+ *   stream   as for fvlbm_init
+ * Step 0 (f = f^eq) runs in every part, then one exchange fills the ghosts.
+ * Errors: as fvlbm_init.
+ */
+typedef struct fvlbm_dd fvlbm_dd;
+int fvlbm_dd_create(const fvlbm_partition* plan, const fvlbm_params* params, int32_t n_params, void* stream,
+                    fvlbm_dd** out);
+/* Advance n time steps: per stage, the stage kernels of every part, then the
+ * exchange.  Asynchronous on the stream.  Errors: FVLBM_ERR_ARG, _CUDA. */
+int fvlbm_dd_step(fvlbm_dd* d, int64_t n);
+/* As fvlbm_macros / fvlbm_get_f / fvlbm_set_f for the whole mesh, in the
+ * caller's numbering of the partitioned mesh (host buffers, synchronise).
+ * fvlbm_dd_set_f also refreshes the ghosts. */
+int fvlbm_dd_macros(fvlbm_dd* d, double* rho, double* u);
+int fvlbm_dd_get_f(fvlbm_dd* d, double* f);
+int fvlbm_dd_set_f(fvlbm_dd* d, const double* f);
+/* Total mass sum_i A_i rho_i (FP64; the parts' sums added in part order).
+ * mass: host [1]. */
+int fvlbm_dd_mass(fvlbm_dd* d, double* mass);
+/* Velocity residual of Sec. 3.2 over the whole mesh (numerator and
+ * denominator summed over the parts in FP64), against the snapshot of the
+ * previous call or of creation; then re-snapshots.  e: host [1]. */
+int fvlbm_dd_residual(fvlbm_dd* d, double* e);
+/* Stage kernel every part runs (as fvlbm_stage_kernel) and launches per step
+ * (stage kernels of all parts plus one exchange kernel per stage). */
+int fvlbm_dd_stage_kernel(const fvlbm_dd* d, int32_t* kernel, int64_t* launches_per_step);
+int fvlbm_dd_sync(fvlbm_dd* d);
+void fvlbm_dd_destroy(fvlbm_dd* d);
 
 /* Message of the last failure on this thread ("" if none). */
 const char* fvlbm_last_error(void);

@@ -62,6 +62,8 @@ def _load():
     lib.orc_run.argtypes = [P, C.c_int, C.c_double, C.c_double, C.c_int64]
     lib.orc_stencil_point.restype = C.c_int
     lib.orc_stencil_point.argtypes = [P, C.c_int64, C.c_int, dp]
+    lib.orc_threads.restype = C.c_int
+    lib.orc_threads.argtypes = [C.c_int]
     lib.orc_cfl_dt.restype = C.c_double
     lib.orc_cfl_dt.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_int]
     _lib = lib
@@ -78,6 +80,12 @@ def _i32(a):
 
 def _i64(a):
     return a.ctypes.data_as(C.POINTER(C.c_int64))
+
+
+def threads(n: int = 0) -> int:
+    """Threads the oracle's loops use from now on (n <= 0: unchanged); returns
+    the number in effect.  A timing control only."""
+    return int(_load().orc_threads(int(n)))
 
 
 def feq(rho: float, ux: float, uy: float) -> np.ndarray:

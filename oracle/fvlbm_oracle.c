@@ -45,6 +45,9 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define Q 9
 
@@ -592,4 +595,18 @@ double orc_cfl_dt(void *hv, double cfl, double umax, double tau, int scheme) {
     double adv = lmin / (sqrt(2.0) + umax);
     double col = scheme == S_AB2 ? tau : 2.0 * tau;
     return cfl * (adv < col ? adv : col);
+}
+
+/*
+ * Timing aid (no arithmetic): threads the OpenMP loops above use from now on
+ * (n <= 0 leaves the setting); returns the number in effect (1 without OpenMP).
+ */
+int orc_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }

@@ -7,11 +7,36 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime_api.h>
 #include <vector_types.h>
 
 #include "fvlbm.h"
 
 namespace fvlbm {
+
+// Makes device d current for the guard's scope and restores the caller's
+// device afterwards (also when the caller's device could not be read: then the
+// device is left as the scope set it, as no previous one is known).
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;   // device d is current
+    explicit DeviceGuard(int d) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        if (prev != d && cudaSetDevice(d) != cudaSuccess) {
+            cudaGetLastError();
+            ok = false;
+        }
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard&) = delete;
+    DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
 
 // ---------------------------------------------------------------- errors
 // Records a message for fvlbm_last_error() and returns `code`.
@@ -48,6 +73,12 @@ constexpr int MAXP = FVLBM_MAX_POLY;
 
 struct Mesh {
     int64_t n_cell = 0;
+    // A part of a partitioned mesh also holds ghost cells: cells [0, n_owned)
+    // (the same in both numberings) are the part's own and are updated; cells
+    // [n_owned, n_grad) are the first ghost ring (their gradient is recomputed
+    // from local data), [n_grad, n_cell) the second (state only).  A whole
+    // mesh has n_owned = n_grad = n_cell.
+    int64_t n_owned = 0, n_grad = 0;
     int32_t max_faces = 0;
     int32_t n_inst = 1;
     std::vector<int64_t> inst_begin;     // [n_inst + 1] cell ranges (same in both numberings)
@@ -102,7 +133,8 @@ constexpr uint32_t LINK_NONE = 0xFFFF;
 
 // Device pointers of one solver (all inside one workspace).
 struct DevView {
-    int64_t n_cell;     // cells (internal numbering 0..n_cell-1)
+    int64_t n_cell;     // cells updated (internal numbering 0..n_cell-1): the owned cells
+    int64_t n_grad;     // cells whose gradient the two-kernel stage computes (owned + first ghost ring)
     int64_t np;         // padded cell count (multiple of the largest tile)
     int64_t n_face;     // face-value table length (two-kernel stage)
     int32_t maxf;       // slots per cell in the packed arrays (4 or 8)
@@ -184,6 +216,17 @@ struct SolverRef {
     int32_t n_inst;
 };
 int solver_ref(fvlbm_solver* s, SolverRef* out);
+// Stages of one time step, and stage k enqueued on the solver's stream (*out:
+// the state buffer it writes); the last stage ends the step.
+int solver_n_stages(const fvlbm_solver* s);
+int solver_stage(fvlbm_solver* s, int k, void** out);
+// FP64 sums of a reduction (RED_MASS: [mass, -, -]; RED_RESIDUAL: [numerator,
+// denominator, -]) per instance, 3 per instance; synchronises.
+int solver_sums(fvlbm_solver* s, int what, std::vector<double>& out);
+// Halo exchange of a partitioned solve: entry e = (src part, src internal
+// cell, dst part, dst internal cell) copies the stored state of one cell from
+// part_state[src] to part_state[dst] (prec = fvlbm_precision of all parts).
+int launch_halo_copy(int prec, void* stream, const int4* entries, int64_t n, void* const* part_state, int n_parts);
 // Reads the solver's non-finite flag after synchronising its stream.
 int solver_sync_check(fvlbm_solver* s);
 
@@ -196,4 +239,32 @@ enum ReduceWhat { RED_MASS = 0, RED_RESIDUAL = 1 };
 
 struct fvlbm_mesh {
     fvlbm::Mesh m;
+};
+
+namespace fvlbm {
+// One part of a partitioned mesh: its cells (caller numbering of the whole
+// mesh) in local order -- owned cells ascending, then ring 1, then ring 2 --
+// and its mesh (owned cells followed by the ghosts).
+struct PartPlan {
+    std::vector<int64_t> cells;
+    int64_t n_owned = 0, n_ring1 = 0, n_ring2 = 0;
+    fvlbm_mesh* mesh = nullptr;
+};
+// The cells part `src` sends to part `dst` after every stage: entry e is the
+// owned cell src_local[e] of src (local numbering) and the ghost dst_local[e]
+// of dst; cells[e] is its number in the whole mesh.
+struct HaloMsg {
+    int32_t src = -1, dst = -1;
+    std::vector<int32_t> src_local, dst_local;
+    std::vector<int64_t> cells;
+};
+}  // namespace fvlbm
+
+struct fvlbm_partition {
+    int32_t n_parts = 0;
+    int64_t n_cell = 0;
+    std::vector<int32_t> owner;            // [n_cell] part owning each cell
+    std::vector<fvlbm::PartPlan> parts;
+    std::vector<fvlbm::HaloMsg> msgs;      // ordered by (src, dst)
+    ~fvlbm_partition();
 };

@@ -18,8 +18,10 @@
 //
 // Precision modes: FP64 keeps f; the deviation modes keep g = f - w and do all
 // arithmetic in FP32 (the flux of the constant w vanishes because the face
-// vectors of a closed cell sum to zero), storing g in FP32, FP16 (times a
-// power-of-two scale per instance and direction) or BF16.
+// vectors of a closed cell sum to zero).  FP32 stores g itself; the 16-bit
+// modes store the split format of fvlbm_device.cuh: rho - 1 and rho u in FP32
+// and the non-equilibrium parts of directions 3..8 in FP16 or BF16, times a
+// power-of-two scale per (instance, direction).
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>

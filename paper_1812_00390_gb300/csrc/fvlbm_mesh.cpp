@@ -88,7 +88,7 @@ static int build_single(const double* xy, int64_t n_vert, const int64_t* cell_pt
         if ((b.kind == FVLBM_BC_INLET || b.kind == FVLBM_BC_OUTLET) && !(b.rho_inf > 0))
             return fail(FVLBM_ERR_ARG, "bc %d: rho_inf must be positive", t);
     }
-    M.n_cell = n_cell;
+    M.n_cell = M.n_owned = M.n_grad = n_cell;
     M.n_inst = 1;
     M.inst_begin = {0, n_cell};
     M.inst_bc_begin = {0, n_bc};
@@ -366,7 +366,7 @@ extern "C" int fvlbm_mesh_concat(const fvlbm_mesh* const* meshes, int32_t n, fvl
             delete r;
             return fail(FVLBM_ERR_ARG, "fvlbm_mesh_concat: too many cells");
         }
-        R.n_cell = nc;
+        R.n_cell = R.n_owned = R.n_grad = nc;
         R.n_inst = 0;
         R.inst_begin = {0};
         R.inst_bc_begin = {0};

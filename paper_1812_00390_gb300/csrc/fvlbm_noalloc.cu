@@ -7,6 +7,13 @@
 // memory is reserved up front by another allocator (a framework's caching pool
 // or a fixed serving budget), and real-time loops or plugins that are not
 // allowed to touch the device heap.  The paper has no counterpart.
+//
+// The array belongs to this file's device module.  With CUDA's default lazy
+// module loading the module, and so the array, is loaded into a device's
+// memory the first time the process uses it there: the first call's
+// cudaGetSymbolAddress.  That first call per device can therefore allocate;
+// callers make it once before the region in which they may not allocate (and
+// before any stream capture).  Later calls allocate nothing.
 #include <mutex>
 
 #include <cuda_runtime.h>
@@ -24,7 +31,8 @@ constexpr int64_t NA_MAX_INST = 4096;     // instances per solver
 constexpr int NA_MAX_DEVICES = 64;
 
 // Partial sums [NA_MAX_CHUNKS], then per-instance results [NA_MAX_INST].
-// Every GPU that loads the library holds these 96 KB until the process exits.
+// Every GPU on which the module is loaded (first call there) holds these 96 KB
+// until the process exits.
 static __device__ __align__(256) double g_noalloc_scratch[NA_MAX_CHUNKS + NA_MAX_INST];
 
 std::mutex g_setup_mutex;
@@ -102,27 +110,23 @@ extern "C" int fvlbm_mass_noalloc(fvlbm_solver* s, double* mass) {
                     "%d instances; limits %lld chunks = %lld cells, %lld instances)",
                     (long long)v.n_chunk, v.n_inst, (long long)NA_MAX_CHUNKS, (long long)(NA_MAX_CHUNKS * 4096),
                     (long long)NA_MAX_INST);
-    int prev = -1;
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != r.device && cudaSetDevice(r.device) != cudaSuccess)
-        return fail(FVLBM_ERR_CUDA, "fvlbm_mass_noalloc: cannot select device %d", r.device);
+    DeviceGuard dg(r.device);
+    if (!dg.ok) return fail(FVLBM_ERR_CUDA, "fvlbm_mass_noalloc: cannot select device %d", r.device);
     double* scratch = nullptr;
     rc = scratch_address(r.device, &scratch);
-    if (rc == FVLBM_OK) {
-        cudaStream_t st = (cudaStream_t)r.stream;
-        double* part = scratch;
-        double* res = scratch + NA_MAX_CHUNKS;
-        switch (r.prec) {
-            case FVLBM_FP64: launch<double, false>(v, st, part, res); break;
-            case FVLBM_FP32_DEV: launch<float, true>(v, st, part, res); break;
-            case FVLBM_FP16_DEV: launch<__half, true>(v, st, part, res); break;
-            default: launch<__nv_bfloat16, true>(v, st, part, res); break;
-        }
-        cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaMemcpyAsync(mass, res, sizeof(double) * v.n_inst, cudaMemcpyDeviceToHost, st);
-        if (e != cudaSuccess) rc = fail(FVLBM_ERR_CUDA, "fvlbm_mass_noalloc: %s", cudaGetErrorString(e));
-        else rc = solver_sync_check(s);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)r.stream;
+    double* part = scratch;
+    double* res = scratch + NA_MAX_CHUNKS;
+    switch (r.prec) {
+        case FVLBM_FP64: launch<double, false>(v, st, part, res); break;
+        case FVLBM_FP32_DEV: launch<float, true>(v, st, part, res); break;
+        case FVLBM_FP16_DEV: launch<__half, true>(v, st, part, res); break;
+        case FVLBM_BF16_DEV: launch<__nv_bfloat16, true>(v, st, part, res); break;
+        default: return fail(FVLBM_ERR_ARG, "fvlbm_mass_noalloc: unknown precision %d", r.prec);
     }
-    if (prev >= 0 && prev != r.device) cudaSetDevice(prev);
-    return rc;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mass, res, sizeof(double) * v.n_inst, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return fail(FVLBM_ERR_CUDA, "fvlbm_mass_noalloc: %s", cudaGetErrorString(e));
+    return solver_sync_check(s);
 }

@@ -44,6 +44,9 @@ struct fvlbm_solver {
     bool pingpong = false;
     void* buf[2] = {nullptr, nullptr};
     int cur = 0;
+    // the 4-stage scheme on the fused stage: a third stage buffer, so that no
+    // stage writes the buffer it reads (the middle stages alternate fb, fc)
+    void* fc = nullptr;
     // CUDA graphs of one step and of GRAPH_CHUNK steps, built lazily, one pair
     // per state buffer the step starts from
     cudaGraphExec_t g1[2] = {nullptr, nullptr}, gk[2] = {nullptr, nullptr};
@@ -54,18 +57,6 @@ struct fvlbm_solver {
 static constexpr int64_t GRAPH_CHUNK = 32;
 
 namespace {
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int d) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != d) cudaSetDevice(d);
-    }
-    ~DeviceGuard() {
-        int cur;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
 
 int cuda_fail(cudaError_t e, const char* what) {
     return fail(FVLBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
@@ -239,10 +230,12 @@ int make_tiles(const Mesh& M, int maxf, int tile, TilePlan& P) {
     TileScratch W;
     W.stamp.assign(n, 0);
     W.loc.assign(n, 0);
+    // tiles cover the owned cells; ghost cells of a partition only appear in halos
+    const int64_t n_own = M.n_owned;
     int64_t c0 = 0;
     int guess = tile;   // neighbouring tiles have similar lengths: start one block above the last
-    while (c0 < n) {
-        int len = (int)std::min<int64_t>(guess, n - c0);
+    while (c0 < n_own) {
+        int len = (int)std::min<int64_t>(guess, n_own - c0);
         int nl = 0, nf = 0;
         while (!try_tile(M, maxf, c0, len, tile, ls, fs, W, nl, nf)) {
             if (len == 1)
@@ -251,7 +244,7 @@ int make_tiles(const Mesh& M, int maxf, int tile, TilePlan& P) {
             len = len > BLK ? (len - 1) / BLK * BLK : len / 2;
         }
         guess = std::min(tile, (len + BLK) / BLK * BLK);
-        if (len < std::min<int64_t>(tile, n - c0)) P.short_tiles++;
+        if (len < std::min<int64_t>(tile, n_own - c0)) P.short_tiles++;
         for (int li = 0; li < len; li++)
             for (int k = 0; k < maxf; k++) {
                 const size_t x = (size_t)li * maxf + k;
@@ -279,7 +272,7 @@ struct Layout {
     int block;
     bool pingpong;   // single-stage scheme on the fused stage: the state alternates between fa and fb
     TilePlan tp;
-    size_t off_desc, off_geo, off_nbr, off_area, off_grp, off_inst, off_bc, off_fa, off_fb, off_rprev, off_fv,
+    size_t off_desc, off_geo, off_nbr, off_area, off_grp, off_inst, off_bc, off_fa, off_fb, off_fc, off_rprev, off_fv,
         off_rho, off_ux, off_uy, off_uold, off_part, off_red, off_conv, off_chunk, off_flag, off_tbegin, off_hptr,
         off_halo, off_r1ptr, off_r1link, off_iperm, total;
 };
@@ -323,13 +316,13 @@ int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L, int 
             int ls = 0, fs = 0;
             size_t smem = 0;
             tile_dims(t, L.maxf, (int)R, ls, fs, smem);
-            if ((M.n_cell + t - 1) / t >= sms && smem <= SMEM_LIMIT) tile = t;
+            if ((M.n_owned + t - 1) / t >= sms && smem <= SMEM_LIMIT) tile = t;
         }
         if (prec == FVLBM_FP64) tile = 0;
     }
     L.strategy = tile == 0 || tile == 1 ? STRATEGY_TWO_KERNEL : STRATEGY_TILE;
     L.block = 256;
-    while (L.block > 32 && (M.n_cell + L.block - 1) / L.block < 2 * sms) L.block /= 2;
+    while (L.block > 32 && (M.n_owned + L.block - 1) / L.block < 2 * sms) L.block /= 2;
     if (L.strategy == STRATEGY_TILE) {
         int ls = 0, fs = 0;
         size_t smem = 0;
@@ -365,6 +358,7 @@ int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L, int 
     L.off_r1link = take(tiled ? 4 * n_r1 * L.maxf : 0);
     L.off_fa = take(S * plane);   // everything before this is uploaded once
     L.off_fb = (scheme == FVLBM_RK2 || scheme == FVLBM_RK4 || L.pingpong) ? take(S * plane) : 0;
+    L.off_fc = (scheme == FVLBM_RK4 && tiled) ? take(S * plane) : 0;
     L.off_rprev = scheme == FVLBM_AB2 ? take(R * plane * FVLBM_Q) : 0;
     L.off_fv = take(two ? R * (size_t)std::max<int64_t>(1, L.n_face) * (FVLBM_Q - 1) : 0);
     L.off_rho = take(8 * plane);
@@ -528,7 +522,7 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
     s->stream = (cudaStream_t)stream;
     s->prec = p0.precision;
     s->scheme = p0.scheme;
-    s->n_cell = M.n_cell;
+    s->n_cell = M.n_owned;
     s->n_inst = M.n_inst;
     s->inst_begin = M.inst_begin;
     int pageable = 0;
@@ -648,7 +642,8 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
     CK(cudaMemsetAsync(base + L.off_flag, 0, 16, s->stream), "clear flag");
 
     DevView& v = s->v;
-    v.n_cell = M.n_cell;
+    v.n_cell = M.n_owned;
+    v.n_grad = M.n_grad;
     v.np = L.np;
     v.n_face = L.n_face;
     v.maxf = L.maxf;
@@ -690,6 +685,7 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
     s->pingpong = L.pingpong;
     s->buf[0] = v.fa;
     s->buf[1] = v.fb;
+    s->fc = L.off_fc ? base + L.off_fc : nullptr;
     s->cur = 0;
 
     // Step 0 and the first residual snapshot
@@ -743,36 +739,55 @@ static void set_current(fvlbm_solver* s, int c) {
     s->v.fb = s->buf[c ^ 1];
 }
 
-// Enqueue one time step.  ev: null, or 3 events per stage (see launch_stage).
-static int enqueue_step(fvlbm_solver* s, void* const* ev = nullptr) {
+// Enqueue stage k of one time step (0 <= k < n_stages).  ev: null, or 3
+// events (see launch_stage).  *out (if not null): the buffer the stage writes.
+// The last stage of a single-stage scheme also ends the step (AB2 history,
+// alternating state).
+static int enqueue_stage(fvlbm_solver* s, int k, void* const* ev, void** out) {
     const DevView& v = s->v;
+    void* dst = nullptr;
+    int rc = FVLBM_OK;
     switch (s->scheme) {
         case FVLBM_EULER:
         case FVLBM_AB2: {
             const int mode = s->scheme == FVLBM_EULER ? MODE_RK : (s->ab2_started ? MODE_AB2 : MODE_AB2_FIRST);
             // in place on the two-kernel stage (each cell reads only its own state
             // after the face values are written); fa -> fb and swap on the fused stage
-            int rc = launch_stage(v, s->prec, s->stream, v.fa, v.fa, s->pingpong ? v.fb : v.fa, 1.0, mode, ev);
+            dst = s->pingpong ? v.fb : v.fa;
+            rc = launch_stage(v, s->prec, s->stream, v.fa, v.fa, dst, 1.0, mode, ev);
             if (rc) return rc;
             if (s->scheme == FVLBM_AB2) s->ab2_started = true;
             if (s->pingpong) set_current(s, s->cur ^ 1);
-            return FVLBM_OK;
+            break;
         }
-        case FVLBM_RK2: {
-            int rc = launch_stage(v, s->prec, s->stream, v.fa, v.fa, v.fb, 0.5, MODE_RK, ev);
-            return rc ? rc : launch_stage(v, s->prec, s->stream, v.fb, v.fa, v.fa, 1.0, MODE_RK, ev ? ev + 3 : ev);
-        }
+        case FVLBM_RK2:
+            dst = k == 0 ? v.fb : v.fa;
+            rc = launch_stage(v, s->prec, s->stream, k == 0 ? v.fa : v.fb, v.fa, dst, k == 0 ? 0.5 : 1.0, MODE_RK, ev);
+            break;
         case FVLBM_RK4: {
             static const double beta[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
-            for (int k = 0; k < 4; k++) {
-                int rc = launch_stage(v, s->prec, s->stream, k == 0 ? v.fa : v.fb, v.fa, k == 3 ? v.fa : v.fb,
-                                      beta[k], MODE_RK, ev ? ev + 3 * k : ev);
-                if (rc) return rc;
-            }
-            return FVLBM_OK;
+            // fa -> fb -> fb -> fb -> fa, or with a third buffer fa -> fb -> fc -> fb -> fa
+            void* const in[4] = {v.fa, v.fb, s->fc ? s->fc : v.fb, v.fb};
+            void* const o[4] = {v.fb, s->fc ? s->fc : v.fb, v.fb, v.fa};
+            dst = o[k];
+            rc = launch_stage(v, s->prec, s->stream, in[k], v.fa, dst, beta[k], MODE_RK, ev);
+            break;
         }
+        default:
+            return fail(FVLBM_ERR_ARG, "bad scheme");
     }
-    return fail(FVLBM_ERR_ARG, "bad scheme");
+    if (out) *out = dst;
+    return rc;
+}
+
+// Enqueue one time step.  ev: null, or 3 events per stage (see launch_stage).
+static int enqueue_step(fvlbm_solver* s, void* const* ev = nullptr) {
+    const int ns = n_stages(s->scheme);
+    for (int k = 0; k < ns; k++) {
+        int rc = enqueue_stage(s, k, ev ? ev + 3 * k : ev, nullptr);
+        if (rc) return rc;
+    }
+    return FVLBM_OK;
 }
 
 extern "C" int fvlbm_profile(fvlbm_solver* s, int64_t n, double* avg_ms, int32_t max_kinds, int32_t* n_kinds,
@@ -949,6 +964,19 @@ static int reduce(fvlbm_solver* s, int what, std::vector<double>& out) {
     CK(cudaMemcpyAsync(out.data(), s->v.red, out.size() * 8, cudaMemcpyDeviceToHost, s->stream), "read sums");
     return sync_and_check(s);
 }
+
+namespace fvlbm {
+int solver_n_stages(const fvlbm_solver* s) { return n_stages(s->scheme); }
+int solver_stage(fvlbm_solver* s, int k, void** out) {
+    if (!s || k < 0 || k >= n_stages(s->scheme)) return fail(FVLBM_ERR_ARG, "solver_stage: bad arguments");
+    DeviceGuard dg(s->device);
+    return enqueue_stage(s, k, nullptr, out);
+}
+int solver_sums(fvlbm_solver* s, int what, std::vector<double>& out) {
+    DeviceGuard dg(s->device);
+    return reduce(s, what, out);
+}
+}  // namespace fvlbm
 
 extern "C" int fvlbm_residual(fvlbm_solver* s, double* e) {
     clear_error();

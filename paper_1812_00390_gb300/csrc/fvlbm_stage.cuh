@@ -270,7 +270,7 @@ __device__ __forceinline__ bool update_cell(const DevView& v, const InstParam& P
 template <typename T, typename S, int MAXF, bool DEV>
 __global__ void __launch_bounds__(256) face_values_kernel(DevView v, const S* __restrict__ fin) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= v.n_cell) return;
+    if (i >= v.n_grad) return;   // owned cells and, in a partition, the first ghost ring
     const GeoRef<T, MAXF> G(v.desc, v.geo, i);
     const int32_t* nb = v.nbr + blk_index(i, MAXF);
     uint2 d[MAXF];
@@ -608,9 +608,9 @@ static int stage_t(const DevView& v, cudaStream_t st, const void* fin, const voi
         return check_launch("fused stage kernel");
     }
     const int bs = v.block > 0 ? v.block : 256;   // smaller blocks spread small meshes over all SMs
-    const unsigned g = grid_of(v.n_cell, bs);
-    if (v.maxf == 4) face_values_kernel<T, S, 4, DEV><<<g, bs, 0, st>>>(v, (const S*)fin);
-    else face_values_kernel<T, S, 8, DEV><<<g, bs, 0, st>>>(v, (const S*)fin);
+    const unsigned g = grid_of(v.n_cell, bs), gg = grid_of(v.n_grad, bs);
+    if (v.maxf == 4) face_values_kernel<T, S, 4, DEV><<<gg, bs, 0, st>>>(v, (const S*)fin);
+    else face_values_kernel<T, S, 8, DEV><<<gg, bs, 0, st>>>(v, (const S*)fin);
     if (ev) cudaEventRecord((cudaEvent_t)ev[1], st);
     if (v.maxf == 4)
         update_kernel<T, S, 4, DEV><<<g, bs, 0, st>>>(v, (const S*)fin, (const S*)fbase, (S*)fout, (T)beta, mode);

@@ -52,6 +52,11 @@ class MeshInfoT(C.Structure):
                 ("total_area", C.c_double), ("min_cfl_length", C.c_double)]
 
 
+class PartInfoT(C.Structure):
+    _fields_ = [("n_owned", C.c_int64), ("n_ring1", C.c_int64), ("n_ring2", C.c_int64),
+                ("n_recv", C.c_int64), ("n_send", C.c_int64), ("n_neighbours", C.c_int32)]
+
+
 class ServerConfigT(C.Structure):
     _fields_ = [("device", C.c_int32), ("n_streams", C.c_int32), ("arena_bytes", C.c_size_t),
                 ("max_active", C.c_int32), ("check_interval", C.c_int32), ("residual_tol", C.c_double),
@@ -75,7 +80,11 @@ EXPORTS = ["fvlbm_mesh_create", "fvlbm_mesh_concat", "fvlbm_mesh_destroy", "fvlb
            "fvlbm_residual", "fvlbm_mass", "fvlbm_mass_noalloc", "fvlbm_get_f", "fvlbm_set_f", "fvlbm_host_transfer", "fvlbm_stage_kernel", "fvlbm_sync",
            "fvlbm_get_dt", "fvlbm_profile", "fvlbm_autotune", "fvlbm_fma_peak", "fvlbm_launches_per_step", "fvlbm_solver_destroy",
            "fvlbm_server_create", "fvlbm_server_submit", "fvlbm_server_poll", "fvlbm_server_request",
-           "fvlbm_server_stats", "fvlbm_server_destroy", "fvlbm_last_error"]
+           "fvlbm_server_stats", "fvlbm_server_destroy", "fvlbm_mesh_partition", "fvlbm_partition_destroy",
+           "fvlbm_partition_info", "fvlbm_partition_cells", "fvlbm_partition_halo", "fvlbm_dd_create",
+           "fvlbm_dd_step", "fvlbm_dd_macros", "fvlbm_dd_get_f", "fvlbm_dd_set_f", "fvlbm_dd_mass",
+           "fvlbm_dd_residual", "fvlbm_dd_stage_kernel", "fvlbm_dd_sync", "fvlbm_dd_destroy",
+           "fvlbm_last_error"]
 
 
 def _load():
@@ -119,6 +128,21 @@ def _load():
         "fvlbm_server_request": [P, C.c_int64, C.POINTER(RequestInfoT), dp, dp],
         "fvlbm_server_stats": [P, C.POINTER(ServerStatsT)],
         "fvlbm_server_destroy": [P],
+        "fvlbm_mesh_partition": [P, C.c_int32, PP],
+        "fvlbm_partition_destroy": [P],
+        "fvlbm_partition_info": [P, C.c_int32, C.POINTER(PartInfoT)],
+        "fvlbm_partition_cells": [P, C.c_int32, i64p],
+        "fvlbm_partition_halo": [P, C.c_int32, C.c_int32, i64p, i32p, i32p],
+        "fvlbm_dd_create": [P, C.POINTER(ParamsT), C.c_int32, P, PP],
+        "fvlbm_dd_step": [P, C.c_int64],
+        "fvlbm_dd_macros": [P, dp, dp],
+        "fvlbm_dd_get_f": [P, dp],
+        "fvlbm_dd_set_f": [P, dp],
+        "fvlbm_dd_mass": [P, dp],
+        "fvlbm_dd_residual": [P, dp],
+        "fvlbm_dd_stage_kernel": [P, i32p, i64p],
+        "fvlbm_dd_sync": [P],
+        "fvlbm_dd_destroy": [P],
         "fvlbm_last_error": [],
     }
     for name, args in sig.items():
@@ -128,6 +152,8 @@ def _load():
     lib.fvlbm_mesh_destroy.restype = None
     lib.fvlbm_solver_destroy.restype = None
     lib.fvlbm_server_destroy.restype = None
+    lib.fvlbm_partition_destroy.restype = None
+    lib.fvlbm_dd_destroy.restype = None
     lib.fvlbm_last_error.restype = C.c_char_p
     return lib
 
@@ -268,6 +294,14 @@ class Solver:
     def macros(self):
         rho = np.zeros(self.n_cell)
         u = np.zeros((self.n_cell, 2))
+        return self.macros_into(rho, u)
+
+    def macros_into(self, rho: np.ndarray, u: np.ndarray):
+        """rho [n_cell] and u [n_cell, 2] (C-contiguous float64 arrays the
+        caller owns, e.g. pinned host memory) written in place."""
+        for a, shape in ((rho, (self.n_cell,)), (u, (self.n_cell, 2))):
+            if a.dtype != np.float64 or a.shape != shape or not a.flags.c_contiguous:
+                raise ValueError(f"macros_into: need a C-contiguous float64 array of shape {shape}")
         _check(lib.fvlbm_macros(self._h, _d(rho), _d(u)))
         return rho, u
 
@@ -362,6 +396,114 @@ def autotune(mesh: Mesh, params, steps: int = 10, stream=None):
     ms = np.zeros(5)
     _check(lib.fvlbm_autotune(mesh._h, arr, len(plist), C.c_void_p(sh), steps, C.byref(best), _d(ms)))
     return best.value, dict(zip(KERNEL_VARIANTS, ms.tolist()))
+
+
+class Partition:
+    """Domain decomposition plan of a one-instance mesh (host only): recursive
+    coordinate bisection into n_parts parts, two ghost rings per part, and the
+    halo messages that fill them after every stage."""
+
+    def __init__(self, mesh: Mesh, n_parts: int):
+        h = C.c_void_p()
+        _check(lib.fvlbm_mesh_partition(mesh._h, int(n_parts), C.byref(h)))
+        self._h = h
+        self.mesh = mesh
+        self.n_parts = int(n_parts)
+        self.n_cell = mesh.n_cell
+
+    def info(self, part: int) -> dict:
+        i = PartInfoT()
+        _check(lib.fvlbm_partition_info(self._h, int(part), C.byref(i)))
+        return {k: getattr(i, k) for k, _ in PartInfoT._fields_}
+
+    def cells(self, part: int) -> np.ndarray:
+        """Whole-mesh cell numbers of the part's local cells: owned, ring 1, ring 2."""
+        i = self.info(part)
+        out = np.zeros(i["n_owned"] + i["n_ring1"] + i["n_ring2"], np.int64)
+        _check(lib.fvlbm_partition_cells(self._h, int(part), out.ctypes.data_as(C.POINTER(C.c_int64))))
+        return out
+
+    def halo(self, src: int, dst: int):
+        """(src_local, dst_local) of the message src sends dst after every stage."""
+        n = C.c_int64()
+        _check(lib.fvlbm_partition_halo(self._h, int(src), int(dst), C.byref(n), None, None))
+        a, b = np.zeros(n.value, np.int32), np.zeros(n.value, np.int32)
+        if n.value:
+            _check(lib.fvlbm_partition_halo(self._h, int(src), int(dst), C.byref(n),
+                                            a.ctypes.data_as(C.POINTER(C.c_int32)),
+                                            b.ctypes.data_as(C.POINTER(C.c_int32))))
+        return a, b
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib.fvlbm_partition_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+class DDSolver:
+    """Partitioned solve of one mesh on one GPU (fvlbm_dd_* in the header): one
+    solver per part of `plan`, the halo exchange after every stage."""
+
+    def __init__(self, plan: Partition, params: ParamsT, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.Stream(device=params.device)
+        self.stream = stream
+        self.plan = plan                      # must outlive the solver
+        self.n_cell = plan.n_cell
+        sh = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+        h = C.c_void_p()
+        _check(lib.fvlbm_dd_create(plan._h, C.byref(params), 1, C.c_void_p(sh), C.byref(h)))
+        self._h = h
+
+    def step(self, n: int = 1):
+        _check(lib.fvlbm_dd_step(self._h, int(n)))
+
+    def sync(self):
+        _check(lib.fvlbm_dd_sync(self._h))
+
+    def macros(self):
+        rho, u = np.zeros(self.n_cell), np.zeros((self.n_cell, 2))
+        _check(lib.fvlbm_dd_macros(self._h, _d(rho), _d(u)))
+        return rho, u
+
+    def get_f(self) -> np.ndarray:
+        f = np.zeros((self.n_cell, 9))
+        _check(lib.fvlbm_dd_get_f(self._h, _d(f)))
+        return f
+
+    def set_f(self, f):
+        f = np.ascontiguousarray(f, np.float64).reshape(self.n_cell, 9)
+        _check(lib.fvlbm_dd_set_f(self._h, _d(f)))
+
+    def mass(self) -> float:
+        m = C.c_double()
+        _check(lib.fvlbm_dd_mass(self._h, C.byref(m)))
+        return m.value
+
+    def residual(self) -> float:
+        e = C.c_double()
+        _check(lib.fvlbm_dd_residual(self._h, C.byref(e)))
+        return e.value
+
+    def stage_kernel(self):
+        """(stage kernel of the parts, kernel launches per time step)."""
+        k, n = C.c_int32(), C.c_int64()
+        _check(lib.fvlbm_dd_stage_kernel(self._h, C.byref(k), C.byref(n)))
+        return k.value, n.value
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib.fvlbm_dd_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 REQ_QUEUED, REQ_ACTIVE, REQ_DONE, REQ_FAILED = 0, 1, 2, 3

@@ -151,10 +151,12 @@ def test_fused_stage_every_scheme(fv, orc, name, scheme, kernel):
     assert rel_err(s.get_f(), o.get_f()) < FP64_TOL
 
 
-@pytest.mark.parametrize("scheme", ["euler", "ab2"])
+@pytest.mark.parametrize("scheme", ["euler", "ab2", "rk4"])
 def test_fused_single_stage_many_tiles(fv, scheme):
-    """A mesh with many more tiles than resident CTAs: the fused stage of a
-    single-stage scheme (ping-pong state) agrees with the two-kernel stage."""
+    """A mesh with many more tiles than resident CTAs, where a tile that
+    updated the buffer it reads would race with tiles still reading it as
+    halo: the fused stage of a single-stage scheme (alternating state) and of
+    the 4-stage scheme (three stage buffers) agrees with the two-kernel stage."""
     m = mg.cavity(500, 8.0)   # 250,000 cells: ~1950 tiles of 128, more than fit on the GPU at once
     p = dict(scheme=scheme, precision="fp32", u0=(0.0, 0.0))
     ref = fv.Solver(fv.Mesh(m), fv.make_params(0.05, kernel=1, **p))
@@ -300,30 +302,6 @@ def test_batch_equals_solo(fv, orc):
         for k, m in enumerate(meshes):
             assert np.array_equal(fb[off:off + m.n_cell], solo[k]), (prec, k)
             off += m.n_cell
-
-
-def test_cavity_mixed_precision_velocity_error(fv, orc):
-    """Lid-driven cavity 128^2 (tanh-stretched, 1:20), Re = 400, RK2, 10^4 steps
-    against the FP64 oracle: FP32 deviation mode within 1e-5 relative velocity
-    error; the 16-bit split formats (FP32 rho, rho u; 16-bit non-equilibrium
-    part) within the bounds stated for them."""
-    m = mg.cavity(128, 20.0, U=0.1)
-    tau = 3 * 0.1 / 400
-    o = orc.Oracle(m)
-    dt = o.cfl_dt(0.5, 0.1, tau, "rk2")
-    n = 10000
-    sol = {p: fv.Solver(fv.Mesh(m), fv.make_params(tau, dt=dt, scheme="rk2", precision=p))
-           for p in ("fp32", "fp16", "bf16")}
-    for s in sol.values():
-        s.step(n)
-    o.set_equilibrium(1.0, (0.0, 0.0))
-    o.run("rk2", tau, dt, n)
-    _, uo = o.macros()
-    err = {p: np.abs(s.macros()[1] - uo).max() / np.abs(uo).max() for p, s in sol.items()}
-    print("cavity relative velocity error after 1e4 steps:", err)
-    assert err["fp32"] < 1e-5, err          # measured 2.8e-6
-    assert err["fp16"] < 1e-3, err          # measured 4.7e-4
-    assert err["bf16"] < 1e-2, err          # measured 4.4e-3
 
 
 @pytest.mark.parametrize("prec,tol", [("fp32", 5e-6), ("fp16", 5e-5), ("bf16", 1e-3)])

@@ -24,7 +24,7 @@ def fv():
     return fvlbm
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
 def test_noalloc_mass_matches_mass_twice(fv, prec):
     parts = [fv.Mesh(mg.cavity(40, 8.0)), fv.Mesh(mg.couette(16, 6)),
              fv.Mesh(mg.cylinder_hybrid(n_rad=20, n_circ=60, first=0.01, growth=1.1, r_far=10.0,
