@@ -245,9 +245,23 @@ __device__ __forceinline__ bool update_cell(const DevView& v, const InstParam& P
             return !bad;
         }
     }
+    // Deviation modes: the collision term f^eq - f carries no mass or momentum
+    // (f^eq has the cell's rho and rho u), so directions 0..2 follow from
+    // directions 3..8 through those identities.  Evaluated directly in FP32,
+    // its nine rounding errors (about eps |g| each, |g| >> |f^eq - f|) would
+    // add a spurious mass and momentum source of about eps |g| / tau per unit
+    // time, which dominated the velocity error at small tau.
+    T col[FVLBM_Q];
+    if constexpr (DEV) {
+#pragma unroll
+        for (int a = 3; a < FVLBM_Q; a++) col[a] = feqs<T, DEV>(a, rho, ux, uy) - f[a];
+        col[1] = col[3] - col[5] + col[6] + col[7] - col[8];
+        col[2] = col[4] - col[5] - col[6] + col[7] + col[8];
+        col[0] = -(col[1] + col[2] + col[3] + col[4] + col[5] + col[6] + col[7] + col[8]);
+    }
 #pragma unroll
     for (int a = 0; a < FVLBM_Q; a++) {
-        const T rhs = -flux[a] - (f[a] - feqs<T, DEV>(a, rho, ux, uy)) * inv_tau;
+        const T rhs = DEV ? -flux[a] + col[a] * inv_tau : -flux[a] - (f[a] - feqs<T, DEV>(a, rho, ux, uy)) * inv_tau;
         if (mode == MODE_RK) {
             out[a] = (use_fb ? fb[a] : f[a]) + beta * dt * rhs;
         } else if (mode == MODE_AB2_FIRST) {
