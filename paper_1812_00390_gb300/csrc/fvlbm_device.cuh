@@ -64,6 +64,11 @@ __device__ __forceinline__ T rarg(double rho) { return DEV ? T(rho - 1.0) : T(rh
 __host__ __device__ __forceinline__ int64_t blk_index(int64_t i, int ncomp) {
     return (i >> BLK_SHIFT) * ((int64_t)ncomp << BLK_SHIFT) + (i & (BLK - 1));
 }
+// The same in 32-bit arithmetic, for the fused stage kernel, whose solvers
+// keep every blocked array below 2^32 elements (checked at set-up).
+__host__ __device__ __forceinline__ uint32_t blk_index(uint32_t i, int ncomp) {
+    return (i >> BLK_SHIFT) * ((uint32_t)ncomp << BLK_SHIFT) + (i & (BLK - 1));
+}
 
 // Whole-cell access to the stored state (T: arithmetic type, DEV: deviation
 // mode, the stored quantity is g = f - w).
@@ -80,14 +85,14 @@ __host__ __device__ __forceinline__ int64_t blk_index(int64_t i, int ncomp) {
 template <typename S> struct CellIO;
 
 template <typename S> struct PlainIO {
-    template <typename T, bool DEV>
-    __device__ static void load(const void* base, int64_t i, const InstParam&, T* f) {
+    template <typename T, bool DEV, typename I>
+    __device__ static void load(const void* base, I i, const InstParam&, T* f) {
         const S* p = (const S*)base + blk_index(i, FVLBM_Q);
 #pragma unroll
         for (int a = 0; a < FVLBM_Q; a++) f[a] = (T)p[a * BLK];
     }
-    template <typename T, bool DEV>
-    __device__ static void store(void* base, int64_t i, const InstParam&, const T* f) {
+    template <typename T, bool DEV, typename I>
+    __device__ static void store(void* base, I i, const InstParam&, const T* f) {
         S* p = (S*)base + blk_index(i, FVLBM_Q);
 #pragma unroll
         for (int a = 0; a < FVLBM_Q; a++) p[a * BLK] = (S)f[a];
@@ -207,7 +212,8 @@ template <typename T, int MAXF> struct GeoRef {
     typedef typename Vec2<T>::type T2;
     const uint2* d;
     const T2* g;
-    __device__ __forceinline__ GeoRef(const void* desc, const void* geo, int64_t i)
+    template <typename I>
+    __device__ __forceinline__ GeoRef(const void* desc, const void* geo, I i)
         : d((const uint2*)desc + blk_index(i, MAXF)), g((const T2*)geo + blk_index(i, 3 * MAXF)) {}
     __device__ __forceinline__ uint2 desc(int k) const { return d[k * BLK]; }
     __device__ __forceinline__ T2 cg(int k) const { return g[(3 * k) * BLK]; }

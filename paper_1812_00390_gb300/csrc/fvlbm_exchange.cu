@@ -28,7 +28,7 @@ __global__ void halo_copy_kernel(const int4* __restrict__ ent, int64_t n, PartPt
     const int4 x = ent[e];   // src part, src cell, dst part, dst cell
     const E* src = (const E*)ptr.p[x.x];
     E* dst = (E*)ptr.p[x.z];
-    dst[blk_index(x.w, C) + c * BLK] = src[blk_index(x.y, C) + c * BLK];
+    dst[blk_index((int64_t)x.w, C) + c * BLK] = src[blk_index((int64_t)x.y, C) + c * BLK];
 }
 
 template <typename E, int C>

@@ -207,6 +207,22 @@ bool try_tile(const Mesh& M, int maxf, int64_t c0, int len, int threads, int ls,
             const int64_t q = internal_nbr(M, W.r1[e], k);
             if (q >= 0) W.r_nb[(size_t)e * maxf + k] = W.loc[q];
         }
+    // Slots without a neighbour (boundary faces, unused slots) link to the
+    // cell itself, so that the kernel's gradient loop needs no test of the
+    // slot kind (the difference to itself is zero); unused slots of tile
+    // cells name face row 0, which they never write (their mask is empty) and
+    // whose values they weight by a zero face vector.
+    for (int li = 0; li < len; li++) {
+        const int nfc = M.nf[M.perm[c0 + li]];
+        for (int k = 0; k < maxf; k++) {
+            const size_t x = (size_t)li * maxf + k;
+            if (W.t_nb[x] < 0) W.t_nb[x] = li;
+            if (k >= nfc) W.t_f[x] = 0;
+        }
+    }
+    for (int e = 0; e < n1; e++)
+        for (int k = 0; k < maxf; k++)
+            if (W.r_nb[(size_t)e * maxf + k] < 0) W.r_nb[(size_t)e * maxf + k] = len + e;
     n_local = nl;
     n_faces = nf;
     return true;
@@ -332,6 +348,11 @@ int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L, int 
                         tile, smem, SMEM_LIMIT);
         int rc = make_tiles(M, L.maxf, tile, L.tp);
         if (rc) return rc;
+        // the fused kernel indexes its blocked arrays in 32 bits
+        const uint64_t lim = (uint64_t)1 << 32;
+        if ((uint64_t)L.np * 3 * L.maxf >= lim || (uint64_t)(L.tp.r1_ptr.back() + BLK) * L.maxf >= lim)
+            return fail(FVLBM_ERR_UNSUPPORTED, "fused stage: %lld cells exceed its 32-bit indexing; use kernel = 1",
+                        (long long)M.n_cell);
     }
     const bool tiled = L.strategy == STRATEGY_TILE, two = !tiled;
     L.pingpong = tiled && (scheme == FVLBM_EULER || scheme == FVLBM_AB2);
@@ -457,7 +478,12 @@ void pack_geometry(const Mesh& M, const Layout& L, std::vector<unsigned char>& h
             const Slot& S = M.slots[(size_t)c * MAXP + k];
             const size_t d = blk(i, k, maxf);
             const int64_t j = S.kind == SK_INTERIOR ? M.iperm[S.nb] : -1;
-            const uint32_t mask = S.kind == SK_INTERIOR ? writer_mask(S, i, k, j) : S.outmask;
+            // the directions this slot writes by reconstruction: on interior
+            // faces the upwind ones (writer_mask), on inlet and internal-outlet
+            // faces the outflow ones; the other boundary faces take ghost values
+            // for every direction, so their mask is empty
+            const bool io = S.kind == SK_INLET || (S.kind == SK_OUTLET && !M.bcs[S.bc].external);
+            const uint32_t mask = S.kind == SK_INTERIOR ? writer_mask(S, i, k, j) : (io ? S.outmask : 0u);
             desc[2 * d] = (uint32_t)S.kind | (mask << 8) | ((uint32_t)(S.bc < 0 ? 0 : S.bc) << 16);
             if (two) {
                 int32_t& f = fid[(size_t)i * maxf + k];
@@ -467,8 +493,6 @@ void pack_geometry(const Mesh& M, const Layout& L, std::vector<unsigned char>& h
                 }
                 desc[2 * d + 1] = (uint32_t)f;
                 nbr[d] = (int32_t)j;
-            } else {
-                desc[2 * d + 1] = L.tp.link[(size_t)i * maxf + k];
             }
             const size_t q0 = blk(i, 3 * k, 3 * maxf), q1 = blk(i, 3 * k + 1, 3 * maxf), q2 = blk(i, 3 * k + 2, 3 * maxf);
             geo[2 * q0] = (T)S.cgx;
@@ -478,6 +502,9 @@ void pack_geometry(const Mesh& M, const Layout& L, std::vector<unsigned char>& h
             geo[2 * q2] = (T)(S.nx / M.area[c]);
             geo[2 * q2 + 1] = (T)(S.ny / M.area[c]);
         }
+        // fused stage: every slot's tile-local links (unused slots included)
+        if (!two)
+            for (int k = 0; k < maxf; k++) desc[2 * blk(i, k, maxf) + 1] = L.tp.link[(size_t)i * maxf + k];
     }
     if (!two) {
         uint32_t* r1 = (uint32_t*)(H + L.off_r1link);

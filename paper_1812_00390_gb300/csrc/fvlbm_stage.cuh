@@ -222,8 +222,8 @@ template <typename T, int MAXF, int STRIDE> struct StagedGeo {
 // (f - f^eq) / tau, then out = base + beta dt rhs (multistage; the base state
 // is fb when use_fb, else f itself) or the AB2 combination.  Returns false
 // when an output is not finite.
-template <typename T, typename S, bool DEV, bool FMA_RK = false>
-__device__ __forceinline__ bool update_cell(const DevView& v, const InstParam& P, int64_t i, const T* f, T rho, T ux,
+template <typename T, typename S, bool DEV, bool FMA_RK = false, typename I>
+__device__ __forceinline__ bool update_cell(const DevView& v, const InstParam& P, I i, const T* f, T rho, T ux,
                                             T uy, const T* flux, const T* fb, bool use_fb, S* fout, T beta,
                                             int mode) {
     const T inv_tau = inst_inv_tau<T>(P);
@@ -339,6 +339,78 @@ __global__ void __launch_bounds__(256) update_kernel(DevView v, const S* __restr
         *v.flag = 1;
 }
 
+// Fused stage, phase 2 for one local cell x (a tile cell, or a 1-ring entry),
+// everything in shared memory: its least-squares gradient (Eq. leastsquare)
+// and its values on the tile's faces.  The planner links every slot without
+// a neighbour (boundary faces, unused slots) to the cell itself, and gives
+// unused slots zero geometry and an empty mask, so the loops over the slots
+// test no slot kind:
+//   1. gradient over all slots from the neighbour differences (zero for the
+//      self-linked slots);
+//   2. only for cells with boundary slots (rare): the ghost differences of
+//      Sec. 2.4.1 enter the gradient, and the boundary face values that are
+//      ghost values are written (Sec. 2.4.2);
+//   3. every slot writes the reconstruction f + grad f . (x_f - x_i)
+//      (Eq. lslrflux) for the directions in its mask: the upwind ones on
+//      interior faces, the outflow ones on inlet and internal-outlet faces,
+//      none elsewhere; a 1-ring entry writes only the faces it shares with
+//      the tile (the others carry no local face).
+template <typename T, bool DEV, int MAXF, int LS, int FS, typename Geo>
+__device__ __forceinline__ void tile_gradient_faces(const uint2* dx, const Geo& H, const BcParam* bcs, const T* fs,
+                                                    T* fvs, int x) {
+    T f[FVLBM_Q];
+#pragma unroll
+    for (int a = 0; a < FVLBM_Q; a++) f[a] = fs[a * LS + x];
+    T gx[FVLBM_Q - 1], gy[FVLBM_Q - 1];
+#pragma unroll
+    for (int a = 0; a < FVLBM_Q - 1; a++) gx[a] = gy[a] = T(0);
+#pragma unroll
+    for (int k = 0; k < MAXF; k++) {
+        const typename Vec2<T>::type c = H.cg(k);
+        const T* p = fs + (dx[k].y & 0xFFFF);
+#pragma unroll
+        for (int a = 1; a < FVLBM_Q; a++) {
+            const T dd = p[a * LS] - f[a];
+            gx[a - 1] += c.x * dd;
+            gy[a - 1] += c.y * dd;
+        }
+    }
+    bool bc = false;
+#pragma unroll
+    for (int k = 0; k < MAXF; k++) bc |= (dx[k].x & 0xFF) > SK_INTERIOR;
+    if (bc) {
+        T rho, ux, uy;
+        moments<T, DEV>(f, rho, ux, uy);
+#pragma unroll
+        for (int k = 0; k < MAXF; k++) {
+            const uint32_t kind = dx[k].x & 0xFF;
+            if (kind <= SK_INTERIOR) continue;
+            const Ghost<T> g = ghost_state<T, DEV>(kind, bcs[dx[k].x >> 16], rho, ux, uy, [&] { return H.nv(k); });
+            const typename Vec2<T>::type c = H.cg(k);
+            const uint32_t mask = (dx[k].x >> 8) & 0xFF;
+            const uint32_t lf = dx[k].y >> 16;
+            T* fo = lf == LINK_NONE ? nullptr : fvs + lf;
+#pragma unroll
+            for (int a = 1; a < FVLBM_Q; a++) {
+                const T dd = ghost_delta<T, DEV>(g, a, f[a], feqs<T, DEV>(a, rho, ux, uy));
+                gx[a - 1] += c.x * dd;
+                gy[a - 1] += c.y * dd;
+                if (fo && !((mask >> (a - 1)) & 1u)) fo[(a - 1) * FS] = g.sym ? f[a] + T(0.5) * dd : f[a] + dd;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < MAXF; k++) {
+        const uint32_t lf = dx[k].y >> 16;
+        const uint32_t mask = lf == LINK_NONE ? 0u : (dx[k].x >> 8) & 0xFF;
+        T* fo = fvs + (lf == LINK_NONE ? 0u : lf);
+        const typename Vec2<T>::type r = H.rv(k);
+#pragma unroll
+        for (int a = 1; a < FVLBM_Q; a++)
+            if ((mask >> (a - 1)) & 1u) fo[(a - 1) * FS] = f[a] + gx[a - 1] * r.x + gy[a - 1] * r.y;
+    }
+}
+
 // Fused stage: one CTA per tile of consecutive cells (Hilbert order; tile
 // and 1-ring together at most TILE cells), everything between the state read
 // and the state write in shared memory:
@@ -369,16 +441,18 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
     T* fs = (T*)smem_raw;            // [9][LS]  f of the local cells
     T* fvs = fs + FVLBM_Q * LS;      // [8][FS]  face values of directions 1..8
     T2* gst = (T2*)(fvs + (FVLBM_Q - 1) * FS);   // [2 MAXF][TILE] cg, rv of each thread's gradient cell
-    const int64_t t = blockIdx.x;
-    const int64_t c0 = v.tile_begin[t];
-    const int nt = (int)(v.tile_begin[t + 1] - c0);
-    const int64_t h0 = v.halo_ptr[t];
-    const int nh = (int)(v.halo_ptr[t + 1] - h0);
-    const int64_t q0 = v.r1_ptr[t];
-    const int n1 = (int)(v.r1_ptr[t + 1] - q0);
+    // cell, halo and 1-ring indices in 32 bits: the set-up keeps every array
+    // of a fused-stage solver below 2^32 elements
+    const uint32_t t = blockIdx.x;
+    const uint32_t c0 = (uint32_t)v.tile_begin[t];
+    const int nt = (int)((uint32_t)v.tile_begin[t + 1] - c0);
+    const uint32_t h0 = (uint32_t)v.halo_ptr[t];
+    const int nh = (int)((uint32_t)v.halo_ptr[t + 1] - h0);
+    const uint32_t q0 = (uint32_t)v.r1_ptr[t];
+    const int n1 = (int)((uint32_t)v.r1_ptr[t + 1] - q0);
     const int l = threadIdx.x;
     const bool mine = l < nt;          // this thread owns tile cell l
-    const int64_t gi = c0 + l;
+    const uint32_t gi = c0 + l;
 
     // phase 1 (thread l's first local cell is local cell l).  The 16-bit split
     // formats are staged raw (moments, packed non-equilibrium words, instance)
@@ -389,9 +463,9 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
     uint32_t* raww = (uint32_t*)(rawc + 3 * LS);   // [3][LS]
     int32_t* rawg = (int32_t*)(raww + 3 * LS);     // [LS]
     static_assert(PLAIN || 7 * LS * 4 <= (FVLBM_Q - 1) * FS * (int)sizeof(T), "raw staging fits the face table");
-    int64_t gl = c0;
+    uint32_t gl = c0;
     for (int x = l; x < nt + nh; x += TILE) {
-        const int64_t gx = x < nt ? c0 + x : (int64_t)v.halo[h0 + (x - nt)];
+        const uint32_t gx = x < nt ? c0 + x : (uint32_t)v.halo[h0 + (x - nt)];
         if (x == l) gl = gx;
         if constexpr (PLAIN) {
             const S* p = fin + blk_index(gx, FVLBM_Q);
@@ -412,9 +486,9 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
     // x: with the planner's bound nt + n1 <= TILE every thread has at most one.
     // Its descriptors and local links are in flight during the wait.
     const int n2 = nt + n1;
-    auto links = [&](int x, int64_t g, uint2* d) {
+    auto links = [&](int x, uint32_t g, uint2* d) {
         const GeoRef<T, MAXF> H(v.desc, v.geo, g);
-        const uint32_t* rl = x < nt ? nullptr : v.r1link + blk_index(q0 + (x - nt), MAXF);
+        const uint32_t* rl = x < nt ? nullptr : v.r1link + blk_index(q0 + (uint32_t)(x - nt), MAXF);
 #pragma unroll
         for (int k = 0; k < MAXF; k++) {
             d[k] = H.desc(k);
@@ -471,67 +545,24 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
     }
 
     // phase 2
-    auto item = [&](int x, int64_t g, const uint2* dx) {
-        const StagedGeo<T, MAXF, TILE> H{gst + x, GeoRef<T, MAXF>(v.desc, v.geo, g)};
-        T f[FVLBM_Q];
-#pragma unroll
-        for (int a = 0; a < FVLBM_Q; a++) f[a] = fs[a * LS + x];
-        T rho, ux, uy;
-        boundary_moments<T, DEV, MAXF>(dx, f, rho, ux, uy);
-        T gx[FVLBM_Q - 1], gy[FVLBM_Q - 1];
-        // tile cells write every face; 1-ring entries only the faces they share
-        // with the tile (their other links hold no local face)
-        auto row = [&](int k) {
-            const uint32_t lf = dx[k].y >> 16;
-            return lf == LINK_NONE ? (T*)nullptr : fvs + lf;
-        };
-        lsq_gradient<T, DEV, MAXF>(dx, H, v.bc, f, rho, ux, uy, gx, gy, [&](int k, T* fj) {
-            const T* p = fs + (dx[k].y & 0xFFFF);
-#pragma unroll
-            for (int a = 1; a < FVLBM_Q; a++) fj[a] = p[a * LS];
-        }, FS, row);
-        write_faces<T, DEV, MAXF>(dx, H, v.bc, f, rho, ux, uy, gx, gy, FS, row);
-    };
-    if (l < n2) item(l, gl, d);
-    // never taken while the planner keeps nt + n1 <= TILE: the staged
-    // geometry has one row per thread
-    for (int x = l + TILE; x < n2; x += TILE) {
-        const int64_t g = (int64_t)v.halo[h0 + (x - nt)];
-        uint2 dx[MAXF];
-        links(x, g, dx);
-        const GeoRef<T, MAXF> H(v.desc, v.geo, g);
-        T f[FVLBM_Q];
-#pragma unroll
-        for (int a = 0; a < FVLBM_Q; a++) f[a] = fs[a * LS + x];
-        T rho, ux, uy;
-        boundary_moments<T, DEV, MAXF>(dx, f, rho, ux, uy);
-        T gx[FVLBM_Q - 1], gy[FVLBM_Q - 1];
-        // tile cells write every face; 1-ring entries only the faces they share
-        // with the tile (their other links hold no local face)
-        auto row = [&](int k) {
-            const uint32_t lf = dx[k].y >> 16;
-            return lf == LINK_NONE ? (T*)nullptr : fvs + lf;
-        };
-        lsq_gradient<T, DEV, MAXF>(dx, H, v.bc, f, rho, ux, uy, gx, gy, [&](int k, T* fj) {
-            const T* p = fs + (dx[k].y & 0xFFFF);
-#pragma unroll
-            for (int a = 1; a < FVLBM_Q; a++) fj[a] = p[a * LS];
-        }, FS, row);
-        write_faces<T, DEV, MAXF>(dx, H, v.bc, f, rho, ux, uy, gx, gy, FS, row);
+    if (l < n2) {
+        const StagedGeo<T, MAXF, TILE> H{gst + l, GeoRef<T, MAXF>(v.desc, v.geo, gl)};
+        tile_gradient_faces<T, DEV, MAXF, LS, FS>(d, H, v.bc, fs, fvs, l);
     }
     // phase 3 inputs, in flight during the wait
     T2 n[MAXF];
     T fb[FVLBM_Q];
     const bool rk_base = mode == MODE_RK && fbase != fin;
-    const GeoRef<T, MAXF> G(v.desc, v.geo, mine ? gi : c0);
     if (mine) {
+        const GeoRef<T, MAXF> G(v.desc, v.geo, gi);
 #pragma unroll
         for (int k = 0; k < MAXF; k++) n[k] = G.nv(k);
         if (rk_base) CellIO<S>::template load<T, DEV>(fbase, gi, v.inst[v.grp[gi]], fb);
     }
     __syncthreads();
 
-    // phase 3
+    // phase 3: flux of every slot from the face table, with no test of the
+    // slot kind (unused slots read face row 0 with a zero face vector)
     if (!mine) return;
     const InstParam& P = v.inst[v.grp[gi]];
     T f[FVLBM_Q];
@@ -540,11 +571,17 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
     T rho, ux, uy;
     moments<T, DEV>(f, rho, ux, uy);
     T flux[FVLBM_Q];
-    flux_sum<T, DEV, MAXF>(d, n, f, flux, [&](int k, T* fa) {
+#pragma unroll
+    for (int a = 0; a < FVLBM_Q; a++) flux[a] = T(0);
+#pragma unroll
+    for (int k = 0; k < MAXF; k++) {
         const T* p = fvs + (d[k].y >> 16);
 #pragma unroll
-        for (int a = 0; a < FVLBM_Q - 1; a++) fa[a] = p[a * FS];
-    });
+        for (int a = 1; a < FVLBM_Q; a++) {
+            const T en = T(EXA(a)) * n[k].x + T(EYA(a)) * n[k].y;
+            flux[a] += en * (DEV ? p[(a - 1) * FS] - f[a] : p[(a - 1) * FS]);
+        }
+    }
     if (!update_cell<T, S, DEV>(v, P, gi, f, rho, ux, uy, flux, fb, rk_base, fout, beta, mode))
         *v.flag = 1;
 }

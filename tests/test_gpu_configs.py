@@ -126,14 +126,17 @@ def test_cavity_re1000_5e4_steps(fv, orc, prec, kernel):
     m = cavity_mesh()
     tau = 3 * 0.1 / 1000
     ref = oracle_case(orc, ("cavity", 1000), m, tau, (0.0, 0.0), 0.1)
-    s = run(fv, m, tau, ref.dt, prec, kernel, (0.0, 0.0), 50_000)
+    s = run(fv, m, tau, ref.dt, prec, kernel, (0.0, 0.0), 49_000)
+    s.residual()                    # snapshot 1000 steps (the residual interval of Sec. 3.2) before the end
+    s.step(1000)
     eu, er = errors(s, ref.at(50_000))
-    print(f"cavity Re 1000 kernel {kernel} {prec} 5e4 steps: rel |u| {eu:.3e} rho {er:.3e}")
+    e = s.residual()[0]
+    print(f"cavity Re 1000 kernel {kernel} {prec} 5e4 steps: rel |u| {eu:.3e} rho {er:.3e} residual {e:.3e}")
     b = BOUND[("cavity", 1000, 50_000)][prec]
     assert eu < b and er < b, (eu, er)
-    # the residual of Sec. 3.2 is finite and small (the flow is still developing)
-    e = s.residual()[0]
-    assert np.isfinite(e)
+    # the flow is still developing after 5x10^4 steps: the residual is finite,
+    # positive and far above the 1e-8 of a converged solve
+    assert np.isfinite(e) and 1e-8 < e < 1.0
     s.close()
 
 
