@@ -339,6 +339,19 @@ __global__ void __launch_bounds__(256) update_kernel(DevView v, const S* __restr
         *v.flag = 1;
 }
 
+// Slots (bit k) that some active thread of the warp uses: a polygon with
+// fewer faces than MAXF leaves its last slots empty, and when every cell of a
+// warp does (a warp of triangles in a 4-slot mesh), the warp skips them as a
+// whole.  Slots 0..2 are always used.
+template <int MAXF>
+__device__ __forceinline__ uint32_t warp_slots(const uint2* d) {
+    uint32_t u = 7u;
+#pragma unroll
+    for (int k = 3; k < MAXF; k++)
+        if ((d[k].x & 0xFF) != SK_NONE) u |= 1u << k;
+    return __reduce_or_sync(__activemask(), u);
+}
+
 // Fused stage, phase 2 for one local cell x (a tile cell, or a 1-ring entry),
 // everything in shared memory: its least-squares gradient (Eq. leastsquare)
 // and its values on the tile's faces.  The planner links every slot without
@@ -364,8 +377,10 @@ __device__ __forceinline__ void tile_gradient_faces(const uint2* dx, const Geo& 
     T gx[FVLBM_Q - 1], gy[FVLBM_Q - 1];
 #pragma unroll
     for (int a = 0; a < FVLBM_Q - 1; a++) gx[a] = gy[a] = T(0);
+    const uint32_t used = warp_slots<MAXF>(dx);
 #pragma unroll
     for (int k = 0; k < MAXF; k++) {
+        if (k >= 3 && !((used >> k) & 1u)) continue;
         const typename Vec2<T>::type c = H.cg(k);
         const T* p = fs + (dx[k].y & 0xFFFF);
 #pragma unroll
@@ -401,6 +416,7 @@ __device__ __forceinline__ void tile_gradient_faces(const uint2* dx, const Geo& 
     }
 #pragma unroll
     for (int k = 0; k < MAXF; k++) {
+        if (k >= 3 && !((used >> k) & 1u)) continue;
         const uint32_t lf = dx[k].y >> 16;
         const uint32_t mask = lf == LINK_NONE ? 0u : (dx[k].x >> 8) & 0xFF;
         T* fo = fvs + (lf == LINK_NONE ? 0u : lf);
@@ -573,8 +589,10 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
     T flux[FVLBM_Q];
 #pragma unroll
     for (int a = 0; a < FVLBM_Q; a++) flux[a] = T(0);
+    const uint32_t used = warp_slots<MAXF>(d);
 #pragma unroll
     for (int k = 0; k < MAXF; k++) {
+        if (k >= 3 && !((used >> k) & 1u)) continue;
         const T* p = fvs + (d[k].y >> 16);
 #pragma unroll
         for (int a = 1; a < FVLBM_Q; a++) {
