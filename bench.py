@@ -20,6 +20,7 @@ has) on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -112,7 +113,7 @@ def config_runs(fv, torch, dev, steps: int = 30):
     out = {}
     for name, m, tau, scheme, prec, u0 in cases:
         h = fv.Mesh(m)
-        best, _ = fv.autotune(h, fv.make_params(tau, scheme=scheme, precision=prec, u0=u0), steps=20)
+        best, tune = fv.autotune(h, fv.make_params(tau, scheme=scheme, precision=prec, u0=u0), steps=64)
         s = fv.Solver(h, fv.make_params(tau, scheme=scheme, precision=prec, u0=u0, kernel=best))
         s.step(5)
         s.sync()
@@ -131,10 +132,44 @@ def config_runs(fv, torch, dev, steps: int = 30):
         b.record(s.stream)
         s.sync()
         warm = a.elapsed_time(b) / (10 * steps)
-        out[name] = {"cells": m.n_cell, "stage_kernel": best, "cold_l2_mcups": m.n_cell / (cold / 1e3) / 1e6,
+        out[name] = {"cells": m.n_cell, "stage_kernel": best,
+                     "autotune_ms_per_step": {str(k): v for k, v in tune.items()},
+                     "cold_l2_mcups": m.n_cell / (cold / 1e3) / 1e6,
                      "warm_l2_mcups": m.n_cell / (warm / 1e3) / 1e6, "cold_ms_per_step": cold,
                      "warm_ms_per_step": warm}
         s.close()
+    return out
+
+
+def error_per_config(fv):
+    """Mixed-precision error at fixed step counts on the single configurations,
+    against the FP64 mode of the same configuration on the GPU (which the
+    tests hold to the FP64 oracle within 1e-12): max relative |u| error (of
+    the largest FP64 speed) and max |rho| error, per storage precision, each
+    run with the automatic stage kernel."""
+    from paper_1812_00390_gb300 import meshgen as mg
+    cav, cyl = mg.cavity(128, 20.0), mg.cylinder_hybrid()
+    cases = [("cavity_128_re400", cav, 3 * 0.1 / 400, (0.0, 0.0), 10_000),
+             ("cavity_128_re1000", cav, 3 * 0.1 / 1000, (0.0, 0.0), 10_000),
+             ("cylinder_60k_re20", cyl, 3 * 0.05 / 20, (0.05, 0.0), 2000),
+             ("cylinder_60k_re40", cyl, 3 * 0.05 / 40, (0.05, 0.0), 10_000),
+             ("cylinder_60k_re100", cyl, 3 * 0.05 / 100, (0.05, 0.0), 2000)]
+    out = {}
+    for name, m, tau, u0, n in cases:
+        h = fv.Mesh(m)
+        ref = fv.Solver(h, fv.make_params(tau, scheme="rk2", precision="fp64", u0=u0))
+        ref.step(n)
+        r64, u64 = ref.macros()
+        ref.close()
+        row = {"cells": m.n_cell, "steps": n, "scheme": "rk2"}
+        for prec in ("fp32", "fp16", "bf16"):
+            s = fv.Solver(h, fv.make_params(tau, scheme="rk2", precision=prec, u0=u0))
+            s.step(n)
+            r, u = s.macros()
+            row[prec] = {"max_rel_velocity": float(np.abs(u - u64).max() / np.abs(u64).max()),
+                         "max_abs_density": float(np.abs(r - r64).max()), "stage_kernel": s.stage_kernel()}
+            s.close()
+        out[name] = row
     return out
 
 
@@ -539,24 +574,37 @@ def run_ours(args):
 
     configs = config_runs(fv, torch, dev) if (args.configs and rank == 0) else None
     roof_syn = roofline_synthetic(fv, torch, peak) if (args.configs and rank == 0) else None
+    errs = error_per_config(fv) if (args.configs and rank == 0) else None
 
     # serving stream (config 5): Poisson arrivals of tandem / single cylinder
-    # solves on the continuous-batching server, p50 / p99 time to completion
+    # solves, plus every fourth request a small cavity that converges, on the
+    # continuous-batching server, swept over the arrival rate; the same
+    # requests (meshes, Reynolds numbers, arrival order) at every rate, their
+    # arrival times scaled by 1 / rate
     serving = None
     if args.serving > 0 and rank == 0:
         from paper_1812_00390_gb300 import serving as sv
-        specs = sv.request_mix(args.serving, seed=390, rate=args.serving_rate)
-        meshes = [sv.build_mesh(sp) for sp in specs]
+        base = sv.request_mix(args.serving, seed=390, rate=1.0, cavity_every=4)
+        meshes = [sv.build_mesh(sp) for sp in base]
         srv = fv.Server(int(args.serving_arena_gb * 1e9), device=dev, n_streams=8, max_active=32,
                         check_interval=1000, residual_tol=1e-8, max_steps=args.serving_steps)
-        lat, infos, wall, cells = sv.run_poisson(srv, fv, specs, meshes)
-        serving = sv.summarize(lat, wall, cells)
-        serving.update({"arrival_rate_per_s": args.serving_rate, "precision": "fp32", "scheme": "rk2",
-                        "stop": f"residual <= 1e-8 (checked every 1000 steps) or {args.serving_steps} steps",
-                        "cells_per_request": [int(m.n_cell) for m in meshes],
-                        "converged": int(sum(1 for x in infos if x["residual"] <= 1e-8)),
-                        "arena_gb": args.serving_arena_gb})
+        per_rate = []
+        for rate in [float(x) for x in args.serving_rates.split(",")]:
+            specs = [dataclasses.replace(sp, arrival=sp.arrival / rate) for sp in base]
+            lat, infos, wall, cells = sv.run_poisson(srv, fv, specs, meshes)
+            row = sv.summarize_rate(infos, specs, wall, cells, 1e-8)
+            row["arrival_rate_per_s"] = rate
+            per_rate.append(row)
         srv.close()
+        serving = {"per_rate": per_rate, "precision": "fp32", "scheme": "rk2",
+                   "requests_per_rate": args.serving,
+                   "stop": f"residual <= 1e-8 (checked every 1000 steps) or {args.serving_steps} steps",
+                   "mix": "3/8 tandem double-cylinder (50k-150k cells), 3/8 single cylinder (20k-60k), "
+                          "1/4 cavity 16x16 at Re 5-10 (converges); cylinders Re U[20, 200]",
+                   "cells_per_request": [int(m.n_cell) for m in meshes],
+                   "latency": "p50/p99 of submission to completion over all requests; converged_*: over the "
+                              "requests that reached the tolerance; queue_*: submission to admission",
+                   "arena_gb": args.serving_arena_gb}
 
     if rank == 0:
         line = {
@@ -589,6 +637,7 @@ def run_ours(args):
                     if e2e_val is not None else None),
             "serving": serving,
             "single_configs": configs,
+            "error_per_config": errs,
             "roofline_synthetic": roof_syn,
             "gpu_launches": launches,
             "clocks": clocks,
@@ -610,8 +659,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--e2e-inner", type=int, default=100)
-    ap.add_argument("--serving", type=int, default=8, help="requests in the serving leg (0 = skip)")
-    ap.add_argument("--serving-rate", type=float, default=2.0, help="Poisson arrivals per second")
+    ap.add_argument("--serving", type=int, default=32, help="requests per arrival rate in the serving leg (0 = skip)")
+    ap.add_argument("--serving-rates", default="1,2,4,8,16", help="Poisson arrival rates per second, swept")
     ap.add_argument("--serving-steps", type=int, default=20000)
     ap.add_argument("--serving-arena-gb", type=float, default=8.0)
     ap.add_argument("--no-configs", dest="configs", action="store_false",

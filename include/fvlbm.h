@@ -107,9 +107,11 @@ typedef struct fvlbm_params {
     double rho0;       /* initial density (Step 0: f = f^eq(rho0, u0)) */
     double u0[2];      /* initial velocity */
     int32_t device;    /* CUDA device ordinal; equal for all instances */
-    int32_t kernel;    /* stage kernel: 0 = automatic (FP64: two kernels; otherwise fused
-                          512-thread tiles when the mesh fills the GPU, smaller tiles or two
-                          kernels for small meshes); 1 = two kernels per stage (face values
+    int32_t kernel;    /* stage kernel: 0 = automatic (FP32 / 16-bit: fused 512-thread tiles
+                          from 512 cells per SM, 256-thread tiles from 64, 128-thread tiles
+                          below; FP64: two kernels from 32 cells per SM, fused 128-thread
+                          tiles below, where one launch per stage matters most);
+                          1 = two kernels per stage (face values
                           through memory); 128, 256, 512 or 1024 = one fused kernel per stage
                           with CTAs of that many threads (a tile holds at most that many
                           cells and 1-ring cells together).  Tile sizes whose shared memory
@@ -307,13 +309,18 @@ int fvlbm_profile(fvlbm_solver* s, int64_t n, double* avg_ms, int32_t max_kinds,
 
 /*
  * Autotuner: time every stage-kernel variant (params.kernel = 1, 128, 256,
- * 512, 1024; variants that do not fit are skipped) on this mesh and parameters for
- * `steps` steps after 2 warm-up steps, each in a temporary solver whose
- * workspace the library allocates and frees, and report the fastest.
+ * 512, 1024; variants that do not fit are skipped) on this mesh and parameters,
+ * each in a temporary solver whose workspace the library allocates and frees:
+ * 3 warm-up steps, then 5 runs of `steps` steps; a variant's time is the
+ * median of the 5.  Reports the fastest, except that among the variants
+ * within 3% (or 2 microseconds per step) of the fastest the automatic choice
+ * (params.kernel = 0) wins, and else the first of 512, 256, 128, 1024, 1, so
+ * that timing noise on small meshes does not flip the pick between equally
+ * fast variants.
  *   stream       as for fvlbm_init
  *   best_kernel  host, written: the value to put in fvlbm_params.kernel
- *   ms_per_step  host [5] or NULL: device ms per step of each variant in the
- *                order above (+inf when skipped)
+ *   ms_per_step  host [5] or NULL: median device ms per step of each variant in
+ *                the order above (+inf when skipped)
  * Errors: FVLBM_ERR_ARG, _CUDA, _UNSUPPORTED (no variant fits).
  */
 int fvlbm_autotune(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t n_params, void* stream,

@@ -309,12 +309,17 @@ constexpr int64_t PLANE_ALIGN = 1024;  // cell arrays hold whole blocks and whol
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 // kernel: 1 two-kernel, 128/256/512/1024 fused with that tile size, 0
-// automatic: FP64 takes the two-kernel stage (it spends fewer FP64 operations);
-// the other precisions take 512-thread tiles (the fastest measured on large
-// batches) when there are enough cells for every SM, else the largest smaller
-// tile that still gives every SM a tile of its own, or the two-kernel stage
-// when even 128-thread tiles would leave SMs idle.  The two-kernel stage
-// shrinks its blocks (down to 32 threads) for the same reason.
+// automatic.  The automatic choice, from measurements on GB300:
+//  - FP32 / 16-bit: 512-thread tiles once the mesh gives every SM a tile of
+//    512 (the fastest on large batches), 256-thread tiles down to a quarter of
+//    the SMs' worth of them (e.g. the 128^2 cavity, the 60k-cell cylinder),
+//    128-thread tiles below: a fused stage launches one kernel per stage where
+//    the two-kernel stage launches two, which is what small meshes wait on;
+//  - FP64: the two-kernel stage (it spends fewer FP64 operations: no 1-ring
+//    gradients, and the FP64 mode is bound by GB300's FP64 units) except on
+//    meshes of fewer than 32 cells per SM, which are launch-bound: fused 128.
+// The two-kernel stage shrinks its blocks (down to 32 threads) so that small
+// meshes still spread over the SMs.
 int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L, int sms) {
     L = Layout{};
     L.np = round_up(M.n_cell, PLANE_ALIGN);
@@ -327,14 +332,17 @@ int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L, int 
         return fail(FVLBM_ERR_ARG, "params.kernel = %d: use 0, 1, 128, 256, 512 or 1024", kernel);
     int tile = kernel;
     if (kernel == 0) {
-        tile = 0;
-        for (int t = 512; t >= 128 && !tile; t /= 2) {
+        const int64_t n = M.n_owned;
+        auto fits = [&](int t) {
             int ls = 0, fs = 0;
             size_t smem = 0;
             tile_dims(t, L.maxf, (int)R, ls, fs, smem);
-            if ((M.n_owned + t - 1) / t >= sms && smem <= SMEM_LIMIT) tile = t;
-        }
-        if (prec == FVLBM_FP64) tile = 0;
+            return smem <= SMEM_LIMIT;
+        };
+        if (prec == FVLBM_FP64) tile = n < 32 * (int64_t)sms ? 128 : 1;
+        else if (n >= 512 * (int64_t)sms && fits(512)) tile = 512;
+        else if (n >= 64 * (int64_t)sms) tile = 256;
+        else tile = 128;
     }
     L.strategy = tile == 0 || tile == 1 ? STRATEGY_TWO_KERNEL : STRATEGY_TILE;
     L.block = 256;
@@ -1091,11 +1099,19 @@ extern "C" int fvlbm_autotune(const fvlbm_mesh* mesh, const fvlbm_params* params
     if (!mesh || !params || n_params <= 0 || steps <= 0 || !best_kernel)
         return fail(FVLBM_ERR_ARG, "fvlbm_autotune: bad arguments");
     static const int32_t cand[5] = {1, 128, 256, 512, 1024};
+    constexpr int REPEATS = 5;
     std::vector<fvlbm_params> p(params, params + n_params);
-    double best = INFINITY;
-    int32_t pick = 0;
+    double med[5];
+    // the automatic choice (params.kernel = 0) for this mesh
+    int32_t automatic = 0;
+    {
+        Layout L;
+        if (make_layout(mesh->m, params[0].precision, params[0].scheme, 0, L, device_sms(params[0].device)) == FVLBM_OK)
+            automatic = L.strategy == STRATEGY_TILE ? L.tp.tile : 1;
+        clear_error();
+    }
     for (int c = 0; c < 5; c++) {
-        if (ms_per_step) ms_per_step[c] = INFINITY;
+        med[c] = INFINITY;
         for (auto& q : p) q.kernel = cand[c];
         fvlbm_solver* sv = nullptr;
         int rc = fvlbm_init(mesh, p.data(), n_params, stream, nullptr, 0, &sv);
@@ -1103,30 +1119,46 @@ extern "C" int fvlbm_autotune(const fvlbm_mesh* mesh, const fvlbm_params* params
         if (rc) return rc;
         DeviceGuard dg(sv->device);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
-        float ms = 0;
-        rc = fvlbm_step(sv, 2);
+        rc = fvlbm_step(sv, 3);   // warm-up: direct launches, then the graphs are built
         if (!rc) rc = fvlbm_sync(sv);
         if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
             rc = fail(FVLBM_ERR_CUDA, "fvlbm_autotune: events");
-        if (!rc) {
+        double t[REPEATS];
+        for (int r = 0; r < REPEATS && !rc; r++) {
+            float ms = 0;
             cudaEventRecord(e0, sv->stream);
             rc = fvlbm_step(sv, steps);
             cudaEventRecord(e1, sv->stream);
             if (!rc) rc = fvlbm_sync(sv);
             if (!rc) cudaEventElapsedTime(&ms, e0, e1);
+            t[r] = ms / steps;
         }
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
         fvlbm_solver_destroy(sv);
         if (rc) return rc;
-        const double per = ms / steps;
-        if (ms_per_step) ms_per_step[c] = per;
-        if (per < best) {
-            best = per;
-            pick = cand[c];
-        }
+        std::sort(t, t + REPEATS);
+        med[c] = t[REPEATS / 2];
     }
-    if (!pick) return fail(FVLBM_ERR_UNSUPPORTED, "fvlbm_autotune: no stage kernel variant fits");
-    *best_kernel = pick;
+    int best = -1;
+    for (int c = 0; c < 5; c++)
+        if (std::isfinite(med[c]) && (best < 0 || med[c] < med[best])) best = c;
+    if (best < 0) return fail(FVLBM_ERR_UNSUPPORTED, "fvlbm_autotune: no stage kernel variant fits");
+    // timing noise must not flip the choice between variants that are as fast:
+    // among those within 3% (or 2 microseconds per step, the launch jitter that
+    // small meshes see) of the fastest median, the automatic choice wins, else
+    // the first in a fixed order
+    static const int32_t pref[5] = {512, 256, 128, 1024, 1};
+    const double lim = std::max(1.03 * med[best], med[best] + 0.002);
+    int pick = -1;
+    for (int c = 0; c < 5; c++)
+        if (cand[c] == automatic && med[c] <= lim) pick = c;
+    for (int q = 0; q < 5 && pick < 0; q++)
+        for (int c = 0; c < 5; c++)
+            if (cand[c] == pref[q] && med[c] <= lim) pick = c;
+    best = pick;
+    if (ms_per_step)
+        for (int c = 0; c < 5; c++) ms_per_step[c] = med[c];
+    *best_kernel = cand[best];
     return FVLBM_OK;
 }

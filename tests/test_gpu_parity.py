@@ -407,11 +407,30 @@ def test_autotune_picks_a_variant(fv):
     m = mg.cavity(48, 5.0)
     best, ms = fv.autotune(fv.Mesh(m), fv.make_params(0.05, scheme="rk2", precision="fp32"), steps=5)
     assert best in fv.KERNEL_VARIANTS
-    assert ms[best] == min(ms.values()) and np.isfinite(ms[best]) and ms[best] > 0
+    # the pick is within 3% (or 2 us per step) of the fastest median; near-ties
+    # go to the automatic choice, then to a fixed preference
+    fastest = min(ms.values())
+    assert ms[best] <= max(1.03 * fastest, fastest + 0.002) and np.isfinite(ms[best]) and ms[best] > 0
     s = fv.Solver(fv.Mesh(m), fv.make_params(0.05, scheme="rk2", precision="fp32", kernel=best))
     assert s.stage_kernel() == best
     s.step(3)
     s.sync()
-    # the automatic choice resolves to one of the variants: FP64 to the two-kernel stage
-    assert fv.Solver(fv.Mesh(m), fv.make_params(0.05, precision="fp32")).stage_kernel() in fv.KERNEL_VARIANTS
-    assert fv.Solver(fv.Mesh(m), fv.make_params(0.05, precision="fp64")).stage_kernel() == 1
+    # the automatic choice (152 SMs): FP32 128-thread tiles below 64 cells per
+    # SM, 256 below 512, 512 above; FP64 the two-kernel stage from 32 cells per SM
+    auto = lambda mesh, prec: fv.Solver(fv.Mesh(mesh), fv.make_params(0.05, precision=prec)).stage_kernel()
+    assert auto(m, "fp32") == 128 and auto(m, "fp64") == 128        # 2,304 cells: launch-bound
+    big = mg.cavity(128, 20.0)                                       # 16,384 cells
+    assert auto(big, "fp32") == 256 and auto(big, "fp64") == 1
+
+
+@pytest.mark.parametrize("prec,scheme,make", [("fp64", "euler", lambda: mg.couette()),
+                                               ("fp32", "rk2", lambda: mg.cavity(128, 20.0))])
+def test_autotune_pick_is_repeatable(fv, prec, scheme, make):
+    """The single-mesh configurations get the same pick on repeated runs (the
+    medians of five timings; near-ties resolved by a fixed preference)."""
+    h = fv.Mesh(make())
+    p = fv.make_params(0.05, scheme=scheme, precision=prec)
+    runs = [fv.autotune(h, p, steps=64) for _ in range(3)]
+    picks = [r[0] for r in runs]
+    print(prec, scheme, "autotune picks", picks, [r[1] for r in runs])
+    assert len(set(picks)) == 1, picks
