@@ -114,10 +114,36 @@ template <typename S> struct PlainIO {
 template <> struct CellIO<double> : PlainIO<double> {};
 template <> struct CellIO<float> : PlainIO<float> {};
 
-template <typename H> __device__ __forceinline__ uint32_t h_bits(float x);
-template <> __device__ __forceinline__ uint32_t h_bits<__half>(float x) { return __half_as_ushort(__float2half_rn(x)); }
-template <> __device__ __forceinline__ uint32_t h_bits<__nv_bfloat16>(float x) {
-    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+// Unbiased (stochastic) rounding of q to the 16-bit format H: the upper of the
+// two neighbouring 16-bit values with probability equal to q's distance from
+// the lower one in units of their gap, else the lower one.  Round to nearest
+// would lose every update smaller than half a 16-bit step, so that a slowly
+// relaxing non-equilibrium part could stay up to about 2^-(p+1) tau / dt of
+// itself away from its value (p = 10 bits in FP16, 7 in BF16); unbiased
+// rounding leaves only zero-mean noise.  The random number is an integer hash
+// of q's own bits and the direction (the "lowbias32" mixing function of
+// C. Wellons' hash-prospector, two multiply-xorshift rounds): it changes
+// whenever q does, and equal inputs round alike, so a cell's result does not
+// depend on where it sits (batch, alone, partitioned).
+__device__ __forceinline__ float sr_uniform(float q, int a) {
+    uint32_t x = __float_as_uint(q) ^ (0x9E3779B9u * (uint32_t)(a + 1));
+    x ^= x >> 16;
+    x *= 0x7FEB352Du;
+    x ^= x >> 15;
+    x *= 0x846CA68Bu;
+    x ^= x >> 16;
+    return (float)(x >> 8) * (1.0f / 16777216.0f);
+}
+template <typename H> __device__ __forceinline__ uint32_t h_bits_sr(float q, int a);
+template <> __device__ __forceinline__ uint32_t h_bits_sr<__half>(float q, int a) {
+    const __half lo = __float2half_rd(q), hi = __float2half_ru(q);
+    const float flo = __half2float(lo), fhi = __half2float(hi);
+    return sr_uniform(q, a) * (fhi - flo) < q - flo ? __half_as_ushort(hi) : __half_as_ushort(lo);
+}
+template <> __device__ __forceinline__ uint32_t h_bits_sr<__nv_bfloat16>(float q, int a) {
+    const __nv_bfloat16 lo = __float2bfloat16_rd(q), hi = __float2bfloat16_ru(q);
+    const float flo = __bfloat162float(lo), fhi = __bfloat162float(hi);
+    return sr_uniform(q, a) * (fhi - flo) < q - flo ? __bfloat16_as_ushort(hi) : __bfloat16_as_ushort(lo);
 }
 template <typename H> __device__ __forceinline__ float h_value(uint32_t bits);
 template <> __device__ __forceinline__ float h_value<__half>(uint32_t bits) {
@@ -185,7 +211,7 @@ template <typename H> struct SplitIO {
         uint32_t bits[FVLBM_Q];
 #pragma unroll
         for (int a = 3; a < FVLBM_Q; a++)
-            bits[a] = h_bits<H>(((float)f[a] - feqs<float, true>(a, dr, ux, uy)) * P.scale[a]);
+            bits[a] = h_bits_sr<H>(((float)f[a] - feqs<float, true>(a, dr, ux, uy)) * P.scale[a], a);
 #pragma unroll
         for (int q = 0; q < 3; q++) wp[q * BLK] = bits[3 + 2 * q] | (bits[4 + 2 * q] << 16);
     }

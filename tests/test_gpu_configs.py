@@ -26,17 +26,18 @@ pytestmark = pytest.mark.gpu
 
 # Stated bounds of the relative velocity error per configuration (the density
 # error must stay below the same number), with the values measured on GB300 in
-# the comments (every stage kernel gives the same to two digits).  FP32 meets
-# the 1e-5 target after 10^4 steps except on the cylinder at Re 40, where the
+# the comments (every stage kernel gives the same to two digits; the 16-bit
+# formats round the stored non-equilibrium part without bias).  FP32 meets the
+# 1e-5 target after 10^4 steps except on the cylinder at Re 40, where the
 # start-up transient amplifies per-step rounding (halving dt there raises the
 # error at equal time, 1.4e-5 -> 7.3e-5, so it is not an operator error).
 BOUND = {
-    ("cavity", 400, 10_000): {"fp32": 1e-5, "fp16": 1e-3, "bf16": 1e-2},     # 1.8e-6, 4.7e-4, 4.4e-3
-    ("cavity", 1000, 10_000): {"fp32": 1e-5, "fp16": 1e-3, "bf16": 1e-2},    # 2.2e-7, 1.3e-4, 1.1e-3
-    ("cavity", 1000, 50_000): {"fp32": 1e-5, "fp16": 1e-3, "bf16": 1e-2},    # 2.4e-7, 3.0e-4, 1.6e-3
-    ("cylinder", 20, 2000): {"fp32": 1e-5, "fp16": 3e-3, "bf16": 3e-2},      # 5.0e-6, 1.4e-3, 1.6e-2
-    ("cylinder", 40, 10_000): {"fp32": 2e-5, "fp16": 1e-3, "bf16": 1e-2},    # 1.4e-5, 7.8e-4, 7.5e-3
-    ("cylinder", 100, 2000): {"fp32": 1e-5, "fp16": 1e-3, "bf16": 1e-2},     # 2.9e-6, 2.3e-4, 2.5e-3
+    ("cavity", 400, 10_000): {"fp32": 1e-5, "fp16": 5e-4, "bf16": 2e-3},     # 1.8e-6, 1.4e-4, 5.6e-4
+    ("cavity", 1000, 10_000): {"fp32": 1e-5, "fp16": 5e-4, "bf16": 2e-3},    # 2.2e-7, 3.1e-5, 1.9e-4
+    ("cavity", 1000, 50_000): {"fp32": 1e-5, "fp16": 5e-4, "bf16": 2e-3},    # 2.4e-7, 1.5e-4, 1.7e-4
+    ("cylinder", 20, 2000): {"fp32": 1e-5, "fp16": 5e-4, "bf16": 2e-3},      # 5.0e-6, 6.0e-5, 4.7e-4
+    ("cylinder", 40, 10_000): {"fp32": 2e-5, "fp16": 5e-4, "bf16": 2e-3},    # 1.4e-5, 8.0e-5, 1.3e-4
+    ("cylinder", 100, 2000): {"fp32": 1e-5, "fp16": 5e-4, "bf16": 2e-3},     # 2.9e-6, 2.1e-5, 1.2e-4
 }
 KERNELS = [1, 128, 256, 512]
 

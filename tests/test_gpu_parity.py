@@ -173,11 +173,13 @@ def test_fused_stage_16bit_formats(fv, orc, prec, scheme, name):
     """The 16-bit split formats through the fused stage (raw staging and decode
     in shared memory; alternating state for Euler / AB2) agree with the
     two-kernel stage, which decodes the same storage from global memory
-    (triangles and quads: 4 slots per cell; polygons: 8).  The two kernels
-    round differently in FP32, which can move a stored 16-bit non-equilibrium
-    component by one 16-bit step (2^-10 of it in FP16, 2^-7 in BF16); with
-    |n| up to ~1e-2 of f here that allows ~1e-5 (FP16) / ~1e-4 (BF16) per
-    flip, hence the bounds, an order above."""
+    (triangles and quads: 4 slots per cell; polygons: 8).  Both store the
+    non-equilibrium part with unbiased rounding whose random number is drawn
+    from the value being stored; the two kernels round differently in FP32, so
+    their stored values take different rounding decisions and the two states
+    differ by the rounding noise (one 16-bit step of a component is ~2e-6 of f
+    in FP16, 8x more in BF16; measured after 36 steps: up to 2.0e-4 FP16,
+    2.6e-3 BF16 relative to max |f|), hence the bounds."""
     m = MESHES[name]()
     tau = 0.15
     dt = orc.Oracle(m).cfl_dt(0.5, 0.1, tau, scheme)
@@ -192,7 +194,7 @@ def test_fused_stage_16bit_formats(fv, orc, prec, scheme, name):
         s.close()
     err = rel_err(out[1], out[0])
     print(name, prec, scheme, "fused vs two-kernel", err)
-    assert err < {"fp16": 1e-4, "bf16": 1e-3}[prec], err
+    assert err < {"fp16": 5e-4, "bf16": 5e-3}[prec], err
 
 
 def test_fused_tiles_span_instances(fv):
