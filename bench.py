@@ -202,6 +202,28 @@ def roofline_synthetic(fv, torch, peak_gbs, steps: int = 20):
                      "algorithmic_gbs": alg / (stage_ms / 1e3) / 1e9,
                      "frac_of_hbm_peak": alg / (stage_ms / 1e3) / 1e9 / peak_gbs}
         s.close()
+    # the same mesh as a partitioned solve on this GPU (recursive bisection,
+    # two ghost rings, one halo exchange per stage), FP32: the cost of the
+    # partitioning itself (a multi-GPU run would place one part per GPU)
+    out["partitioned_fp32"] = {}
+    for parts in (2, 4):
+        plan = fv.Partition(h, parts)
+        dd = fv.DDSolver(plan, fv.make_params(0.1, scheme="rk2", precision="fp32", u0=(0.02, 0.01)))
+        dd.step(3)
+        dd.sync()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(dd.stream)
+        dd.step(steps)
+        e.record(dd.stream)
+        dd.sync()
+        ms = a.elapsed_time(e) / steps
+        ghosts = sum(plan.info(p)["n_recv"] for p in range(parts))
+        out["partitioned_fp32"][str(parts)] = {
+            "mcups": m.n_cell / (ms / 1e3) / 1e6, "ms_per_step": ms,
+            "relative_to_undivided": out["fp32"]["ms_per_step"] / ms,
+            "ghost_cells": ghosts, "launches_per_step": dd.stage_kernel()[1]}
+        dd.close()
+        plan.close()
     return out
 
 

@@ -433,7 +433,8 @@ __device__ __forceinline__ void tile_gradient_faces(const uint2* dx, const Geo& 
 //   phase 1  cp.async of the state of the tile, its 1-ring and its 2-ring
 //            (the 16-bit formats raw, decoded after the barrier), and of the
 //            least-squares and reconstruction vectors of each thread's
-//            gradient cell; its slot descriptors into registers
+//            gradient cell and the instance id of each tile cell; the slot
+//            descriptors into registers
 //   phase 2  per tile and 1-ring cell (one per thread): the gradient
 //            (Eq. leastsquare) and its values on the tile's faces
 //            (Eq. lslrflux / Sec. 2.4.2): on interior faces the directions it
@@ -457,6 +458,7 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
     T* fs = (T*)smem_raw;            // [9][LS]  f of the local cells
     T* fvs = fs + FVLBM_Q * LS;      // [8][FS]  face values of directions 1..8
     T2* gst = (T2*)(fvs + (FVLBM_Q - 1) * FS);   // [2 MAXF][TILE] cg, rv of each thread's gradient cell
+    int32_t* sgrp = (int32_t*)(gst + 2 * MAXF * TILE);   // [TILE] instance of each tile cell
     // cell, halo and 1-ring indices in 32 bits: the set-up keeps every array
     // of a fused-stage solver below 2^32 elements
     const uint32_t t = blockIdx.x;
@@ -511,6 +513,7 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
             if (x >= nt) d[k].y = rl[k * BLK];   // the 1-ring entry's local links
         }
     };
+    if (l < nt) cp_async_elem<int32_t>(sgrp + l, v.grp + c0 + l);
     uint2 d[MAXF];
     if (l < n2) {
         links(l, gl, d);
@@ -580,7 +583,7 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
     // phase 3: flux of every slot from the face table, with no test of the
     // slot kind (unused slots read face row 0 with a zero face vector)
     if (!mine) return;
-    const InstParam& P = v.inst[v.grp[gi]];
+    const InstParam& P = v.inst[sgrp[l]];
     T f[FVLBM_Q];
 #pragma unroll
     for (int a = 0; a < FVLBM_Q; a++) f[a] = fs[a * LS + l];
