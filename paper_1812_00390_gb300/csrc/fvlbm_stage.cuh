@@ -271,8 +271,12 @@ __device__ __forceinline__ bool update_cell(const DevView& v, const InstParam& P
             out[a] = f[a] + dt * (T(1.5) * rhs - T(0.5) * rp[a * v.np + i]);
             rp[a * v.np + i] = rhs;
         }
-        bad |= !finite_val(out[a]);
     }
+    // one test: the sum of the outputs is not finite when any output is not
+    T sum = out[0];
+#pragma unroll
+    for (int a = 1; a < FVLBM_Q; a++) sum += out[a];
+    bad = !finite_val(sum);
     CellIO<S>::template store<T, DEV>(fout, i, P, out);
     return !bad;
 }
