@@ -129,8 +129,70 @@ struct TileScratch {
     std::vector<int32_t> loc;
     std::vector<int64_t> r1, r2;
     std::vector<int32_t> t_nb, t_f, r_nb, r_f;
+    std::vector<int32_t> bank_cnt, face_groups, face_row;   // bank_faces
     int64_t gen = 0;
 };
+
+// Face-table rows of a tile chosen for the shared-memory banks (4-byte banks,
+// 32 of them: row r lies in bank r mod 32).  A warp reaches, through one
+// slot, the faces of its 32 cells at once (phase 2 writes them, phase 3 reads
+// them); faces that share a bank there are served one after the other.  Each
+// face, in the order numbered, takes the bank that the fewest faces of its
+// warps' slot groups already hold (ties: the emptiest bank, room permitting),
+// and row bank + 32 * (faces already in that bank); face 0 keeps row 0, which
+// unused slots read (with a zero weight: it must hold finite values, and
+// every row of a face is written in full).  The rows are only addresses: the
+// arithmetic does not change.
+void bank_faces(const Mesh& M, int maxf, int64_t c0, int len, int fs, int nf, TileScratch& W) {
+    const int n1 = (int)W.r1.size();
+    const int depth = fs / BLK;   // rows per bank
+    const int n_groups = (len + n1 + BLK - 1) / BLK * maxf;
+    W.bank_cnt.assign((size_t)n_groups * BLK, 0);
+    W.face_groups.assign((size_t)nf * 2, -1);   // a face is reached through at most two slots
+    auto add = [&](int f, int g) {
+        int* fg = &W.face_groups[(size_t)f * 2];
+        if (fg[0] < 0) fg[0] = g;
+        else if (fg[0] != g) fg[1] = g;
+    };
+    for (int li = 0; li < len; li++) {
+        const int nfc = M.nf[M.perm[c0 + li]];
+        for (int k = 0; k < maxf; k++) {
+            const int g = li / BLK * maxf + k;
+            if (k < nfc) add(W.t_f[(size_t)li * maxf + k], g);
+            else W.bank_cnt[(size_t)g * BLK] = 1;
+        }
+    }
+    for (int e = 0; e < n1; e++)
+        for (int k = 0; k < maxf; k++) {
+            const int f = W.r_f[(size_t)e * maxf + k];
+            if (f >= 0) add(f, (len + e) / BLK * maxf + k);
+        }
+    int load[BLK] = {0};
+    W.face_row.resize(nf);
+    for (int f = 0; f < nf; f++) {
+        const int* fg = &W.face_groups[(size_t)f * 2];
+        int best = 0, best_cost = -1;
+        // face 0 keeps row 0, the row unused slots read: it is written in full
+        for (int b = f == 0 ? BLK : 0; b < BLK; b++) {
+            if (load[b] >= depth) continue;
+            int c = 0;
+            for (int q = 0; q < 2; q++)
+                if (fg[q] >= 0) c += W.bank_cnt[(size_t)fg[q] * BLK + b];
+            c = c * (depth + 1) + load[b];
+            if (best_cost < 0 || c < best_cost) {
+                best_cost = c;
+                best = b;
+            }
+        }
+        for (int q = 0; q < 2; q++)
+            if (fg[q] >= 0) W.bank_cnt[(size_t)fg[q] * BLK + best]++;
+        W.face_row[f] = best + BLK * load[best]++;
+    }
+    for (int32_t& x : W.t_f)
+        if (x >= 0) x = W.face_row[x];
+    for (int32_t& x : W.r_f)
+        if (x >= 0) x = W.face_row[x];
+}
 
 // Local numbering of the tile [c0, c0 + len): tile cells, 1-ring, 2-ring, and
 // the local faces of the tile cells.  False when it exceeds ls / fs, or when
@@ -202,6 +264,7 @@ bool try_tile(const Mesh& M, int maxf, int64_t c0, int len, int threads, int ls,
         }
     }
     if (nf > fs) return false;
+    bank_faces(M, maxf, c0, len, fs, nf, W);
     for (int e = 0; e < n1; e++)
         for (int k = 0; k < M.nf[M.perm[W.r1[e]]]; k++) {
             const int64_t q = internal_nbr(M, W.r1[e], k);
