@@ -115,9 +115,8 @@ typedef struct fvlbm_params {
                           through memory); 128, 256, 512 or 1024 = one fused kernel per stage
                           with CTAs of that many threads (a tile holds at most that many
                           cells and 1-ring cells together).  Tile sizes whose shared memory
-                          exceeds a CTA's (FP64: 1024; FP64 meshes with cells of more than 4
-                          faces: 512 and 1024; FP32/16-bit meshes with cells of more than 4
-                          faces: 1024) give FVLBM_ERR_UNSUPPORTED.  Equal for all instances. */
+                          exceeds a CTA's (FP64: 1024) give FVLBM_ERR_UNSUPPORTED.  Equal for
+                          all instances. */
 } fvlbm_params;
 
 typedef struct fvlbm_mesh_info_s {

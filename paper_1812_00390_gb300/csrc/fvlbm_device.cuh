@@ -238,6 +238,7 @@ template <typename T, int MAXF> struct GeoRef {
     typedef typename Vec2<T>::type T2;
     const uint2* d;
     const T2* g;
+    __device__ __forceinline__ GeoRef() {}
     template <typename I>
     __device__ __forceinline__ GeoRef(const void* desc, const void* geo, I i)
         : d((const uint2*)desc + blk_index(i, MAXF)), g((const T2*)geo + blk_index(i, 3 * MAXF)) {}

@@ -119,15 +119,13 @@ constexpr int BLK = 1 << BLK_SHIFT;
 // Fused stage: shared-memory capacity of a tile of TILE threads (compile-time
 // strides, so that every shared-memory access is a fixed offset from one
 // index): LS local cells (tile, 1-ring, 2-ring), FS local faces (the faces of
-// the tile's cells), for the cell each thread computes a gradient for, its
-// least-squares and reconstruction vectors (2 MAXF pairs of reals of RSIZE
-// bytes), and the instance id of each tile cell.  The tile planner ends a
-// tile early when it would not fit.
+// the tile's cells) and the instance id of each tile cell; reals of RSIZE
+// bytes.  The tile planner ends a tile early when it would not fit.
 template <int TILE, int MAXF, int RSIZE> struct TileDims {
     static constexpr int LS = (3 * TILE) / 2 + 64;
     static constexpr int FS = MAXF <= 4 ? 2 * TILE : (7 * TILE) / 2;
     static constexpr size_t BYTES =
-        (size_t)RSIZE * ((size_t)FVLBM_Q * LS + (size_t)(FVLBM_Q - 1) * FS + (size_t)4 * MAXF * TILE) + (size_t)4 * TILE;
+        (size_t)RSIZE * ((size_t)FVLBM_Q * LS + (size_t)(FVLBM_Q - 1) * FS) + (size_t)4 * TILE;
 };
 // "no local face / neighbour" in a 16-bit link field
 constexpr uint32_t LINK_NONE = 0xFFFF;

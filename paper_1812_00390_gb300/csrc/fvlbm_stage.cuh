@@ -196,25 +196,28 @@ __device__ __forceinline__ void prefetch_l2(const void* p, int64_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"((uint32_t)bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-template <typename V>
-__device__ __forceinline__ void cp_async_vec(V* dst, const V* src) {
-    static_assert(sizeof(V) == 8 || sizeof(V) == 16, "8- or 16-byte vector");
-    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
-    if constexpr (sizeof(V) == 8)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
-}
-
-// Geometry of a cell whose least-squares and reconstruction vectors were
-// staged in shared memory (slot k: cg at k * STRIDE, rv at (MAXF + k) *
-// STRIDE); face vectors (boundary slots only) from global memory.
-template <typename T, int MAXF, int STRIDE> struct StagedGeo {
+// Geometry of a fused-stage gradient cell: with up to 4 slots its
+// least-squares vectors in registers (loaded before the staging barrier; 8
+// slots would spill), else and for its reconstruction and face vectors from
+// global memory (through L1, which the small shared-memory footprint leaves
+// large).
+template <typename T, int MAXF> struct RegGeo {
     typedef typename Vec2<T>::type T2;
-    const T2* s;
+    static constexpr bool REGS = MAXF <= 4;
+    T2 c[REGS ? MAXF : 1];
     GeoRef<T, MAXF> G;
-    __device__ __forceinline__ T2 cg(int k) const { return s[k * STRIDE]; }
-    __device__ __forceinline__ T2 rv(int k) const { return s[(MAXF + k) * STRIDE]; }
+    __device__ __forceinline__ void load(const void* desc, const void* geo, uint32_t i) {
+        G = GeoRef<T, MAXF>(desc, geo, i);
+        if constexpr (REGS) {
+#pragma unroll
+            for (int k = 0; k < MAXF; k++) c[k] = G.cg(k);
+        }
+    }
+    __device__ __forceinline__ T2 cg(int k) const {
+        if constexpr (REGS) return c[k];
+        else return G.cg(k);
+    }
+    __device__ __forceinline__ T2 rv(int k) const { return G.rv(k); }
     __device__ __forceinline__ T2 nv(int k) const { return G.nv(k); }
 };
 
@@ -374,8 +377,7 @@ __device__ __forceinline__ uint32_t warp_slots(const uint2* d) {
 //      the tile (the others carry no local face).
 template <typename T, bool DEV, int MAXF, int LS, int FS, typename Geo>
 __device__ __forceinline__ void tile_gradient_faces(const uint2* dx, const Geo& H, const BcParam* bcs, const T* fs,
-                                                    T* fvs, int x) {
-    T f[FVLBM_Q];
+                                                    T* fvs, int x, T* f) {
 #pragma unroll
     for (int a = 0; a < FVLBM_Q; a++) f[a] = fs[a * LS + x];
     T gx[FVLBM_Q - 1], gy[FVLBM_Q - 1];
@@ -435,23 +437,27 @@ __device__ __forceinline__ void tile_gradient_faces(const uint2* dx, const Geo& 
 // and 1-ring together at most TILE cells), everything between the state read
 // and the state write in shared memory:
 //   phase 1  cp.async of the state of the tile, its 1-ring and its 2-ring
-//            (the 16-bit formats raw, decoded after the barrier), and of the
-//            least-squares and reconstruction vectors of each thread's
-//            gradient cell and the instance id of each tile cell; the slot
-//            descriptors into registers
+//            (the 16-bit formats raw, decoded after the barrier) and of the
+//            instance id of each tile cell; the slot descriptors and the
+//            least-squares vectors of each thread's gradient cell into
+//            registers
 //   phase 2  per tile and 1-ring cell (one per thread): the gradient
 //            (Eq. leastsquare) and its values on the tile's faces
 //            (Eq. lslrflux / Sec. 2.4.2): on interior faces the directions it
 //            writes (upwind side), on boundary faces (tile cells) every
 //            direction -- one writer per (face, direction), into a table of
-//            the tile's faces
+//            the tile's faces; a tile cell's thread keeps its state
 //   phase 3  per tile cell: flux sum from the face table, collision and the
 //            time update (Eq. rhs, Sec. 2.3)
 // The global loads of each phase are issued before the barrier that precedes
 // it, so that their latency overlaps the wait, and each CTA prefetches into L2
 // the data of a tile that starts about one CTA lifetime later (pf = resident
-// CTAs ahead).  Shared-memory strides are compile-time constants (TileDims);
-// the planner keeps every tile within them.
+// CTAs ahead).  The kernel is bound by shared-memory traffic more than by
+// DRAM: what a thread can hold in registers (its own state, its least-squares
+// vectors) or read through L1 (reconstruction and face vectors) stays out of
+// shared memory, whose small footprint leaves L1 large.  Shared-memory
+// strides are compile-time constants (TileDims); the planner keeps every tile
+// within them.
 template <typename T, typename S, int MAXF, bool DEV, int TILE>
 __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0 ? (sizeof(T) == 4 ? 1024 : 512) / TILE : 1)
     stage_tile_kernel(DevView v, const S* __restrict__ fin, const S* fbase, S* fout, T beta, int mode, int pf) {
@@ -461,8 +467,7 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* fs = (T*)smem_raw;            // [9][LS]  f of the local cells
     T* fvs = fs + FVLBM_Q * LS;      // [8][FS]  face values of directions 1..8
-    T2* gst = (T2*)(fvs + (FVLBM_Q - 1) * FS);   // [2 MAXF][TILE] cg, rv of each thread's gradient cell
-    int32_t* sgrp = (int32_t*)(gst + 2 * MAXF * TILE);   // [TILE] instance of each tile cell
+    int32_t* sgrp = (int32_t*)(fvs + (FVLBM_Q - 1) * FS);   // [TILE] instance of each tile cell
     // cell, halo and 1-ring indices in 32 bits: the set-up keeps every array
     // of a fused-stage solver below 2^32 elements
     const uint32_t t = blockIdx.x;
@@ -519,14 +524,10 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
     };
     if (l < nt) cp_async_elem<int32_t>(sgrp + l, v.grp + c0 + l);
     uint2 d[MAXF];
+    RegGeo<T, MAXF> H;
     if (l < n2) {
         links(l, gl, d);
-        const GeoRef<T, MAXF> H(v.desc, v.geo, gl);
-#pragma unroll
-        for (int k = 0; k < MAXF; k++) {
-            cp_async_vec<T2>(gst + k * TILE + l, &H.g[(3 * k) * BLK]);
-            cp_async_vec<T2>(gst + (MAXF + k) * TILE + l, &H.g[(3 * k + 1) * BLK]);
-        }
+        H.load(v.desc, v.geo, gl);
     }
     // The CTA that starts when this one ends works on about tile t + pf (pf =
     // CTAs resident on the GPU): bring that tile's state and geometry into L2
@@ -567,10 +568,10 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
         __syncthreads();
     }
 
-    // phase 2
+    // phase 2 (a tile cell's thread keeps its state for phase 3)
+    T f[FVLBM_Q];
     if (l < n2) {
-        const StagedGeo<T, MAXF, TILE> H{gst + l, GeoRef<T, MAXF>(v.desc, v.geo, gl)};
-        tile_gradient_faces<T, DEV, MAXF, LS, FS>(d, H, v.bc, fs, fvs, l);
+        tile_gradient_faces<T, DEV, MAXF, LS, FS>(d, H, v.bc, fs, fvs, l, f);
     }
     // phase 3 inputs, in flight during the wait
     T2 n[MAXF];
@@ -588,9 +589,6 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
     // slot kind (unused slots read face row 0 with a zero face vector)
     if (!mine) return;
     const InstParam& P = v.inst[sgrp[l]];
-    T f[FVLBM_Q];
-#pragma unroll
-    for (int a = 0; a < FVLBM_Q; a++) f[a] = fs[a * LS + l];
     T rho, ux, uy;
     moments<T, DEV>(f, rho, ux, uy);
     T flux[FVLBM_Q];

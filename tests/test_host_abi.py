@@ -106,9 +106,9 @@ def test_init_without_gpu_fails_loudly(fv):
 
 def test_stage_kernel_capacity_on_the_host(fv):
     """The layout and the fused stage's tile plan are built on the host: every
-    variant that fits a CTA's shared memory gives a workspace; the tile sizes
-    that would not fit (FP64 1024-thread tiles, FP64 hexagon tiles of 512,
-    hexagon tiles of 1024) are refused with FVLBM_ERR_UNSUPPORTED."""
+    variant that fits a CTA's shared memory gives a workspace; the tile size
+    that would not fit (FP64 1024-thread tiles, quads or hexagons) is refused
+    with FVLBM_ERR_UNSUPPORTED."""
     def ws(mesh, prec, kernel):
         arr = (fv.ParamsT * 1)(fv.make_params(0.1, scheme="rk2", precision=prec, kernel=kernel))
         n = C.c_size_t()
@@ -126,7 +126,7 @@ def test_stage_kernel_capacity_on_the_host(fv):
         assert sizes[512] < sizes[1]
     assert ws(quads, "fp32", 1024)[0] == "OK"
     assert ws(quads, "fp64", 1024)[0] == "UNSUPPORTED"
-    assert ws(hexes, "fp64", 256)[0] == "OK"
-    assert ws(hexes, "fp64", 512)[0] == "UNSUPPORTED"
-    assert ws(hexes, "fp32", 1024)[0] == "UNSUPPORTED"
+    assert ws(hexes, "fp64", 512)[0] == "OK"
+    assert ws(hexes, "fp64", 1024)[0] == "UNSUPPORTED"
+    assert ws(hexes, "fp32", 1024)[0] == "OK"
     assert ws(quads, "fp32", 384)[0] == "ARG"
