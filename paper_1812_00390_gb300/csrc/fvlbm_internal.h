@@ -109,6 +109,9 @@ struct BcParam {
     int32_t kind;      // SlotKind of the tag
     int32_t external;
     double uwx, uwy, rho_inf, uix, uiy;
+    // the same rounded to FP32 on the host (rdev_f = rho_inf - 1 in FP64,
+    // then rounded), so that FP32 kernels do no FP64 arithmetic
+    float uwx_f, uwy_f, rho_f, rdev_f, uix_f, uiy_f;
 };
 
 // Per-cell arrays on the device are blocked: 32 consecutive cells per block,

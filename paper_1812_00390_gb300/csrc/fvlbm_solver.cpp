@@ -722,6 +722,12 @@ static int init_impl(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t
         q.rho_inf = c.rho_inf;
         q.uix = c.u_inf[0];
         q.uiy = c.u_inf[1];
+        q.uwx_f = (float)q.uwx;
+        q.uwy_f = (float)q.uwy;
+        q.rho_f = (float)q.rho_inf;
+        q.rdev_f = (float)(q.rho_inf - 1.0);
+        q.uix_f = (float)q.uix;
+        q.uiy_f = (float)q.uiy;
     }
     std::vector<int64_t> chunks;
     for (int32_t k = 0; k < M.n_inst; k++)

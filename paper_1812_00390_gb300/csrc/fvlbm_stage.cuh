@@ -30,22 +30,39 @@ template <typename T> struct Ghost {
     bool io;      // inlet / internal outlet: faces the cell flows out through are reconstructed
 };
 
+// Boundary constants in the arithmetic type (FP32: rounded on the host).
+template <typename T> struct BcVal;
+template <> struct BcVal<double> {
+    static __device__ __forceinline__ double uwx(const BcParam& b) { return b.uwx; }
+    static __device__ __forceinline__ double uwy(const BcParam& b) { return b.uwy; }
+    static __device__ __forceinline__ double uix(const BcParam& b) { return b.uix; }
+    static __device__ __forceinline__ double uiy(const BcParam& b) { return b.uiy; }
+    template <bool DEV> static __device__ __forceinline__ double rho(const BcParam& b) { return rarg<double, DEV>(b.rho_inf); }
+};
+template <> struct BcVal<float> {
+    static __device__ __forceinline__ float uwx(const BcParam& b) { return b.uwx_f; }
+    static __device__ __forceinline__ float uwy(const BcParam& b) { return b.uwy_f; }
+    static __device__ __forceinline__ float uix(const BcParam& b) { return b.uix_f; }
+    static __device__ __forceinline__ float uiy(const BcParam& b) { return b.uiy_f; }
+    template <bool DEV> static __device__ __forceinline__ float rho(const BcParam& b) { return DEV ? b.rdev_f : b.rho_f; }
+};
+
 template <typename T, bool DEV, typename NormalFn>
 __device__ __forceinline__ Ghost<T> ghost_state(uint32_t kind, const BcParam& b, T rho, T ux, T uy, NormalFn normal) {
     Ghost<T> g{rho, ux, uy, false, false, false};
     if (kind == SK_WALL) {
-        g.ux = T(b.uwx);
-        g.uy = T(b.uwy);
+        g.ux = BcVal<T>::uwx(b);
+        g.uy = BcVal<T>::uwy(b);
     } else if (kind == SK_INLET) {
-        if (b.external) g.r = rarg<T, DEV>(b.rho_inf);
-        g.ux = T(b.uix);
-        g.uy = T(b.uiy);
+        if (b.external) g.r = BcVal<T>::template rho<DEV>(b);
+        g.ux = BcVal<T>::uix(b);
+        g.uy = BcVal<T>::uiy(b);
         g.io = true;
     } else if (kind == SK_OUTLET) {
         if (b.external) {
             g.zero = true;
         } else {
-            g.r = rarg<T, DEV>(b.rho_inf);
+            g.r = BcVal<T>::template rho<DEV>(b);
             g.io = true;
         }
     } else {   // symmetry: the face's unit normal is needed only here
