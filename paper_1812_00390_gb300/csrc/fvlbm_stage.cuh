@@ -468,8 +468,8 @@ __device__ __forceinline__ void tile_gradient_faces(const uint2* dx, const Geo& 
 //            time update (Eq. rhs, Sec. 2.3)
 // The global loads of each phase are issued before the barrier that precedes
 // it, so that their latency overlaps the wait, and each CTA prefetches into L2
-// the data of a tile that starts about one CTA lifetime later (pf = resident
-// CTAs ahead).  The kernel is bound by shared-memory traffic more than by
+// the data of a tile that starts somewhat under one CTA lifetime later (pf =
+// 5/8 of the resident CTAs ahead).  The kernel is bound by shared-memory traffic more than by
 // DRAM: what a thread can hold in registers (its own state, its least-squares
 // vectors) or read through L1 (reconstruction and face vectors) stays out of
 // shared memory, whose small footprint leaves L1 large.  Shared-memory
@@ -546,9 +546,10 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
         links(l, gl, d);
         H.load(v.desc, v.geo, gl);
     }
-    // The CTA that starts when this one ends works on about tile t + pf (pf =
-    // CTAs resident on the GPU): bring that tile's state and geometry into L2
-    // now, so that its staging reads L2 rather than HBM.  The last thread does
+    // A CTA that starts somewhat before this one ends works on about tile
+    // t + pf (pf = 5/8 of the CTAs resident on the GPU): bring that tile's
+    // state and geometry into L2 now, so that its staging reads L2 rather than
+    // HBM.  The last thread does
     // it once its own copies are in flight, so that the loads of the other
     // tile's bounds overlap them.
     if (l == TILE - 1 && pf > 0 && t + pf < v.n_tiles) {
@@ -644,9 +645,11 @@ static int tile_launch(const DevView& v, cudaStream_t st, const void* fin, const
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return fail(FVLBM_ERR_CUDA, "fused stage: %zu B shared memory: %s", smem, cudaGetErrorString(e));
     }
-    // prefetch distance: the CTAs that fit on the GPU at once (queried once per
-    // kernel; a function-local static is initialised once even when several
-    // host threads launch at the same time)
+    // prefetch distance: 5/8 of the CTAs that fit on the GPU at once (queried
+    // once per kernel; a function-local static is initialised once even when
+    // several host threads launch at the same time).  Measured on GB300 over
+    // 0.5 to 1.5 times the resident CTAs: 0.6 to 0.75 was best, longer
+    // distances let the prefetched lines age out of L2 before their tile runs.
     static const int per_sm = [&] {
         int n = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, TILE, smem) != cudaSuccess) {
@@ -655,7 +658,7 @@ static int tile_launch(const DevView& v, cudaStream_t st, const void* fin, const
         }
         return n;
     }();
-    const int pf = per_sm * v.sms;
+    const int pf = per_sm * v.sms * 5 / 8;
     kern<<<(unsigned)v.n_tiles, TILE, smem, st>>>(v, (const S*)fin, (const S*)fbase, (S*)fout, (T)beta, mode, pf);
     return FVLBM_OK;
 }
