@@ -120,30 +120,42 @@ template <> struct CellIO<float> : PlainIO<float> {};
 // would lose every update smaller than half a 16-bit step, so that a slowly
 // relaxing non-equilibrium part could stay up to about 2^-(p+1) tau / dt of
 // itself away from its value (p = 10 bits in FP16, 7 in BF16); unbiased
-// rounding leaves only zero-mean noise.  The random number is an integer hash
-// of q's own bits and the direction (the "lowbias32" mixing function of
-// C. Wellons' hash-prospector, two multiply-xorshift rounds): it changes
-// whenever q does, and equal inputs round alike, so a cell's result does not
-// depend on where it sits (batch, alone, partitioned).
-__device__ __forceinline__ float sr_uniform(float q, int a) {
-    uint32_t x = __float_as_uint(q) ^ (0x9E3779B9u * (uint32_t)(a + 1));
+// rounding leaves only zero-mean noise.  It is done on the bits: a uniform
+// random integer below one 16-bit step, in units of q's last FP32 bit, is
+// added to q's magnitude and the sum is truncated (rounded toward zero) to the
+// 16-bit grid, which rounds up exactly when the random number reaches the
+// step minus q's remainder.  That holds for every finite FP32 value in BF16
+// (16 dropped bits, the same exponent range) and for FP16 normals (13 dropped
+// bits); below 2^-14, where FP16's grid spacing is fixed at 2^-24, the two
+// neighbours are compared with the random fraction instead.
+// The random word of a cell comes from one integer hash of the bits of its
+// six rounded values (the "lowbias32" mixing function of C. Wellons'
+// hash-prospector, two multiply-xorshift rounds), spread over the directions
+// by odd multipliers: it changes whenever the cell's values do, and equal
+// cells round alike, so a cell's result does not depend on where it sits
+// (batch, alone, partitioned).
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
     x ^= x >> 16;
     x *= 0x7FEB352Du;
     x ^= x >> 15;
     x *= 0x846CA68Bu;
     x ^= x >> 16;
-    return (float)(x >> 8) * (1.0f / 16777216.0f);
+    return x;
 }
-template <typename H> __device__ __forceinline__ uint32_t h_bits_sr(float q, int a);
-template <> __device__ __forceinline__ uint32_t h_bits_sr<__half>(float q, int a) {
+// random word of direction a from the cell's hash: the high bits of an odd multiple
+__device__ __forceinline__ uint32_t sr_word(uint32_t h, int a) { return h * (0x9E3779B9u + 2u * (uint32_t)a); }
+template <typename H> __device__ __forceinline__ uint32_t h_bits_sr(float q, uint32_t rnd);
+template <> __device__ __forceinline__ uint32_t h_bits_sr<__half>(float q, uint32_t rnd) {
+    const uint32_t b = __float_as_uint(q);
+    if ((b & 0x7F800000u) >= (113u << 23))   // |q| >= 2^-14: FP16 normal, 13 dropped bits
+        return __half_as_ushort(__float2half_rz(__uint_as_float(b + (rnd >> 19))));
     const __half lo = __float2half_rd(q), hi = __float2half_ru(q);
     const float flo = __half2float(lo), fhi = __half2float(hi);
-    return sr_uniform(q, a) * (fhi - flo) < q - flo ? __half_as_ushort(hi) : __half_as_ushort(lo);
+    return (float)(rnd >> 8) * (1.0f / 16777216.0f) * (fhi - flo) < q - flo ? __half_as_ushort(hi)
+                                                                             : __half_as_ushort(lo);
 }
-template <> __device__ __forceinline__ uint32_t h_bits_sr<__nv_bfloat16>(float q, int a) {
-    const __nv_bfloat16 lo = __float2bfloat16_rd(q), hi = __float2bfloat16_ru(q);
-    const float flo = __bfloat162float(lo), fhi = __bfloat162float(hi);
-    return sr_uniform(q, a) * (fhi - flo) < q - flo ? __bfloat16_as_ushort(hi) : __bfloat16_as_ushort(lo);
+template <> __device__ __forceinline__ uint32_t h_bits_sr<__nv_bfloat16>(float q, uint32_t rnd) {
+    return (__float_as_uint(q) + (rnd >> 16)) >> 16;
 }
 template <typename H> __device__ __forceinline__ float h_value(uint32_t bits);
 template <> __device__ __forceinline__ float h_value<__half>(uint32_t bits) {
@@ -208,10 +220,17 @@ template <typename H> struct SplitIO {
         c[BLK] = jx;
         c[2 * BLK] = jy;
         const float inv_rho = 1.0f / (1.0f + dr), ux = jx * inv_rho, uy = jy * inv_rho;
+        float q[FVLBM_Q];
+        uint32_t h = 0x811C9DC5u;
+#pragma unroll
+        for (int a = 3; a < FVLBM_Q; a++) {
+            q[a] = ((float)f[a] - feqs<float, true>(a, dr, ux, uy)) * P.scale[a];
+            h = (h ^ __float_as_uint(q[a])) * 0x01000193u;
+        }
+        h = mix32(h);
         uint32_t bits[FVLBM_Q];
 #pragma unroll
-        for (int a = 3; a < FVLBM_Q; a++)
-            bits[a] = h_bits_sr<H>(((float)f[a] - feqs<float, true>(a, dr, ux, uy)) * P.scale[a], a);
+        for (int a = 3; a < FVLBM_Q; a++) bits[a] = h_bits_sr<H>(q[a], sr_word(h, a));
 #pragma unroll
         for (int q = 0; q < 3; q++) wp[q * BLK] = bits[3 + 2 * q] | (bits[4 + 2 * q] << 16);
     }
