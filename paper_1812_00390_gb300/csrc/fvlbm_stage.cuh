@@ -574,7 +574,9 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
         range(v.r1link, (v.r1_ptr[tp] >> BLK_SHIFT) * LB, ((v.r1_ptr[tp + 1] + BLK - 1) >> BLK_SHIFT) * LB);
     }
     cp_async_wait_all();
-    __syncthreads();
+    // a 16-bit state is decoded by the thread that staged it (its own copies
+    // are complete after the wait), so one barrier serves both
+    if constexpr (PLAIN) __syncthreads();
     if constexpr (!PLAIN) {
         for (int x = l; x < nt + nh; x += TILE) {
             const uint32_t w[3] = {raww[x], raww[LS + x], raww[2 * LS + x]};
