@@ -95,6 +95,17 @@ def tune_kernel(fv, handles, inst, precision, scheme="rk2", n_sample=64, steps=2
     return fv.autotune(mesh, params, steps=steps)
 
 
+def tile_plan_summary(fv, mesh, inst, kernel):
+    """The fused stage's tile plan of the batch (fvlbm_plan_info, on the host):
+    tiles, cells per tile, the 1-ring cells whose gradients each tile
+    recomputes, and the modelled shared-memory wavefronts per warp access."""
+    params = [fv.make_params(tau, scheme="rk2", precision="fp32", u0=u0, kernel=kernel) for _, tau, u0 in inst]
+    i = fv.plan_info(mesh, params)
+    keep = ("stage_kernel", "n_tiles", "mean_tile_cells", "mean_ring1_cells", "mean_local_cells",
+            "max_local_cells", "max_faces", "face_table_waves", "gather_waves", "violations")
+    return {k: i[k] for k in keep}
+
+
 # ----------------------------------------------------------------------------- single configs
 def config_runs(fv, torch, dev, steps: int = 30):
     """MCUPS of the single-mesh configurations.  Their state fits in L2, so every
@@ -573,6 +584,8 @@ def run_ours(args):
             "dram_frac": (traffic_pc * n_cells / (stage_ms / 1e3) / 1e9 / peak if traffic_pc else None),
             "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
             else f"{peak_src} {HBM_FALLBACK_GBS:.0f} GB/s"}
+    if kernel32 != 1:
+        roof["tile_plan"] = tile_plan_summary(fv, s32.mesh, inst, kernel32)
 
     # end to end through the C ABI with host buffers: each e2e step uploads the
     # state from host memory (set_f), advances e2e_inner time steps and reads

@@ -187,6 +187,42 @@ int fvlbm_workspace_bytes(const fvlbm_mesh* mesh, const fvlbm_params* params, in
                           size_t* bytes);
 
 /*
+ * The stage plan fvlbm_init would build (on the host; no GPU needed), checked.
+ * The fused stage's tiles are runs of consecutive cells whose state, 1-ring
+ * and 2-ring sit in a CTA's shared memory, with a table of the tile's face
+ * values (the gradient of Eq. leastsquare and the reconstruction of
+ * Eq. lslrflux stay on chip; Sec. 2.4 algorithm Steps 1-5 in one kernel).
+ * The check covers what the kernel relies on: every slot names its
+ * neighbour's local cell (boundary and unused slots the cell itself, unused
+ * slots face row 0), both sides of a face name one face row and no two faces
+ * share one, each (face, direction) between local cells has exactly one writer
+ * (Sec. 2.4.2: the upwind side), and every tile fits its CTA.  The wavefront
+ * figures model the shared-memory bank conflicts of the kernel's warp
+ * accesses: the most distinct addresses one of the 32 banks receives, averaged
+ * over the accesses (1: conflict-free).
+ *   params: host, [n_params] as for fvlbm_init.  info: host, written.
+ * A failed check is counted in info->violations and described by
+ * fvlbm_last_error(); the call still returns FVLBM_OK.
+ * Errors: FVLBM_ERR_ARG, _OOM, _UNSUPPORTED (as fvlbm_workspace_bytes).
+ */
+typedef struct fvlbm_plan_info_s {
+    int32_t stage_kernel;        /* 1: two kernels per stage; else the fused stage's threads per CTA */
+    int32_t slots;               /* face slots per cell in the packed arrays (4 or 8) */
+    int64_t n_tiles;             /* fused stage: tiles (0 for two kernels) */
+    int64_t short_tiles;         /* tiles cut below the CTA size by the shared-memory capacity */
+    int32_t max_local_cells;     /* largest tile: its cells, 1-ring and 2-ring */
+    int32_t max_faces;           /* largest tile: faces of its cells */
+    double mean_tile_cells;      /* cells per tile */
+    double mean_ring1_cells;     /* 1-ring cells per tile (gradients recomputed) */
+    double mean_local_cells;     /* tile + 1-ring + 2-ring cells per tile */
+    double face_table_waves;     /* wavefronts per warp read of the face table (phase 3) */
+    double gather_waves;         /* wavefronts per warp gather of neighbour state (phase 2) */
+    int64_t violations;          /* failed checks (0) */
+} fvlbm_plan_info_t;
+int fvlbm_plan_info(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t n_params,
+                    fvlbm_plan_info_t* info);
+
+/*
  * Create a solver on params[0].device and set f = f^eq(rho0, u0) (Step 0).
  *   params     host, one entry per instance of the mesh, or one entry for all
  *   n_params   1 or the mesh's instance count

@@ -7,6 +7,7 @@
 // that reads results back (macros, residual, mass, f) synchronises and maps
 // cells back to the caller's numbering.
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -98,6 +99,13 @@ struct TilePlan {
     std::vector<uint32_t> r1link;   // [1-ring entries][maxf] same fields
     int32_t max_local = 0, max_faces = 0;
     int64_t short_tiles = 0;        // tiles cut below `tile` cells by the capacity
+    int64_t sum_len = 0, sum_ring1 = 0, sum_local = 0;   // over the tiles
+    // filled when the plan is verified (fvlbm_plan_info): modelled
+    // shared-memory wavefronts of the warp accesses, and failed invariants
+    bool verify = false;
+    double face_groups = 0, face_waves = 0, gather_groups = 0, gather_waves = 0;
+    int64_t violations = 0;
+    std::string first_violation;
 };
 
 int64_t internal_nbr(const Mesh& M, int64_t i, int k) {
@@ -295,13 +303,129 @@ uint32_t pack_link(int nb, int f) {
     return (uint32_t)(nb < 0 ? LINK_NONE : (uint32_t)nb) | ((uint32_t)(f < 0 ? LINK_NONE : (uint32_t)f) << 16);
 }
 
-int make_tiles(const Mesh& M, int maxf, int tile, TilePlan& P) {
+uint32_t writer_mask(const Slot& S, int64_t i, int k, int64_t j);
+
+// Shared-memory wavefronts of one warp access (4-byte banks, 32 of them):
+// the most distinct addresses that fall into one bank.
+int bank_waves(const int* idx, int n) {
+    int v[BLK];
+    for (int q = 0; q < n; q++) v[q] = idx[q];
+    std::sort(v, v + n);
+    int cnt[BLK] = {0}, m = 0;
+    for (int q = 0; q < n; q++)
+        if (q == 0 || v[q] != v[q - 1]) m = std::max(m, ++cnt[v[q] & (BLK - 1)]);
+    return m;
+}
+
+// Checks of one tile's plan (fvlbm_plan_info): every slot links to its
+// neighbour's local index (boundary and unused slots to the cell itself, unused
+// slots to face row 0), the two sides of a face name one row and no two faces
+// share one, every (face, direction) between local cells has exactly one
+// writer, and tile + 1-ring and the local cells fit the CTA; then the modelled
+// wavefronts of phase 3's face-table reads and phase 2's neighbour gathers.
+void verify_tile(const Mesh& M, int maxf, int64_t c0, int len, int threads, int ls, int fs, int nl,
+                 const TileScratch& W, TilePlan& P) {
+    auto bad = [&](const char* what, int64_t cell) {
+        if (P.violations++ == 0) {
+            char b[200];
+            std::snprintf(b, sizeof b, "tile at cell %lld: %s (cell %lld)", (long long)c0, what, (long long)cell);
+            P.first_violation = b;
+        }
+    };
+    const int n1 = (int)W.r1.size();
+    if (len + n1 > threads) bad("tile and 1-ring exceed the CTA's threads", c0);
+    if (nl > ls) bad("local cells exceed the shared-memory capacity", c0);
+    auto slot = [&](int64_t i, int k) -> const Slot& { return M.slots[(size_t)M.perm[i] * MAXP + k]; };
+    // a face is named by its side with the lower (cell, slot)
+    auto face_key = [&](int64_t i, int k) {
+        const Slot& S = slot(i, k);
+        if (S.kind == SK_INTERIOR) {
+            const int64_t j = M.iperm[S.nb];
+            if (j < i || (j == i && S.nb_slot < k)) return std::make_pair(j, S.nb_slot);
+        }
+        return std::make_pair(i, k);
+    };
+    std::vector<std::pair<int64_t, int>> owner((size_t)fs, std::make_pair((int64_t)-1, -1));
+    for (int li = 0; li < len; li++) {
+        const int64_t i = c0 + li;
+        const int nfc = M.nf[M.perm[i]];
+        for (int k = 0; k < maxf; k++) {
+            const size_t x = (size_t)li * maxf + k;
+            if (k >= nfc) {
+                if (W.t_nb[x] != li || W.t_f[x] != 0) bad("unused slot not linked to itself and row 0", i);
+                continue;
+            }
+            const int row = W.t_f[x];
+            if (row < 0 || row >= fs) {
+                bad("face row outside the table", i);
+                continue;
+            }
+            const auto key = face_key(i, k);
+            if (owner[row].first < 0) owner[row] = key;
+            else if (owner[row] != key) bad("two faces share a face row", i);
+            const Slot& S = slot(i, k);
+            if (S.kind != SK_INTERIOR) {
+                if (W.t_nb[x] != li) bad("boundary slot not linked to itself", i);
+                continue;
+            }
+            const int64_t j = M.iperm[S.nb];
+            const int lj = W.loc[j];
+            if (W.t_nb[x] != lj) bad("slot not linked to its neighbour", i);
+            int other = -2;
+            if (lj < len) other = W.t_f[(size_t)lj * maxf + S.nb_slot];
+            else if (lj < len + n1) other = W.r_f[(size_t)(lj - len) * maxf + S.nb_slot];
+            else bad("a tile cell's neighbour is not in the tile or its 1-ring", i);
+            if (other != -2 && other != row) bad("the two sides of a face name different rows", i);
+            const uint32_t mi = writer_mask(S, i, k, j), mj = writer_mask(slot(j, S.nb_slot), j, S.nb_slot, i);
+            if ((mi & mj) != 0 || (mi | mj) != 0xFFu) bad("a (face, direction) without exactly one writer", i);
+        }
+    }
+    for (int e = 0; e < n1; e++) {
+        const int64_t j = W.r1[e];
+        const int nfc = M.nf[M.perm[j]];
+        for (int k = 0; k < maxf; k++) {
+            const int64_t q = k < nfc ? internal_nbr(M, j, k) : -1;
+            const int want = q >= 0 ? W.loc[q] : len + e;
+            if (W.r_nb[(size_t)e * maxf + k] != want) bad("1-ring slot not linked to its neighbour", j);
+        }
+    }
+    // modelled wavefronts of the warp accesses through one slot (used slots only)
+    int idx[BLK];
+    for (int w = 0; w * BLK < len; w++)
+        for (int k = 0; k < maxf; k++) {
+            int n = 0;
+            bool used = k < 3;
+            for (int li = w * BLK; li < std::min(len, (w + 1) * BLK); li++) {
+                idx[n++] = W.t_f[(size_t)li * maxf + k];
+                used |= k < M.nf[M.perm[c0 + li]];
+            }
+            if (!used) continue;
+            P.face_groups += 1;
+            P.face_waves += bank_waves(idx, n);
+        }
+    for (int w = 0; w * BLK < len + n1; w++)
+        for (int k = 0; k < maxf; k++) {
+            int n = 0;
+            bool used = k < 3;
+            for (int l = w * BLK; l < std::min(len + n1, (w + 1) * BLK); l++) {
+                const int64_t c = l < len ? c0 + l : W.r1[l - len];
+                idx[n++] = l < len ? W.t_nb[(size_t)l * maxf + k] : W.r_nb[(size_t)(l - len) * maxf + k];
+                used |= k < M.nf[M.perm[c]];
+            }
+            if (!used) continue;
+            P.gather_groups += 1;
+            P.gather_waves += bank_waves(idx, n);
+        }
+}
+
+int make_tiles(const Mesh& M, int maxf, int tile, TilePlan& P, bool verify) {
     int ls = 0, fs = 0;
     size_t bytes = 0;
     if (!tile_dims(tile, maxf, 4, ls, fs, bytes)) return fail(FVLBM_ERR_ARG, "unsupported tile size %d", tile);
     const int64_t n = M.n_cell;
     P = TilePlan{};
     P.tile = tile;
+    P.verify = verify;
     P.begin.push_back(0);
     P.halo_ptr.push_back(0);
     P.r1_ptr.push_back(0);
@@ -324,6 +448,10 @@ int make_tiles(const Mesh& M, int maxf, int tile, TilePlan& P) {
         }
         guess = std::min(tile, (len + BLK) / BLK * BLK);
         if (len < std::min<int64_t>(tile, n_own - c0)) P.short_tiles++;
+        P.sum_len += len;
+        P.sum_ring1 += (int64_t)W.r1.size();
+        P.sum_local += nl;
+        if (verify) verify_tile(M, maxf, c0, len, tile, ls, fs, nl, W, P);
         for (int li = 0; li < len; li++)
             for (int k = 0; k < maxf; k++) {
                 const size_t x = (size_t)li * maxf + k;
@@ -383,7 +511,7 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 //    meshes of fewer than 32 cells per SM, which are launch-bound: fused 128.
 // The two-kernel stage shrinks its blocks (down to 32 threads) so that small
 // meshes still spread over the SMs.
-int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L, int sms) {
+int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L, int sms, bool verify = false) {
     L = Layout{};
     L.np = round_up(M.n_cell, PLANE_ALIGN);
     L.n_face = M.n_face;
@@ -417,7 +545,7 @@ int make_layout(const Mesh& M, int prec, int scheme, int kernel, Layout& L, int 
         if (smem > SMEM_LIMIT)
             return fail(FVLBM_ERR_UNSUPPORTED, "fused stage with %d-cell tiles needs %zu B of shared memory (limit %zu)",
                         tile, smem, SMEM_LIMIT);
-        int rc = make_tiles(M, L.maxf, tile, L.tp);
+        int rc = make_tiles(M, L.maxf, tile, L.tp, verify);
         if (rc) return rc;
         // the fused kernel indexes its blocked arrays in 32 bits
         const uint64_t lim = (uint64_t)1 << 32;
@@ -602,6 +730,43 @@ extern "C" int fvlbm_workspace_bytes(const fvlbm_mesh* mesh, const fvlbm_params*
     }
     if (rc) return rc;
     *bytes = L.total;
+    return FVLBM_OK;
+}
+
+extern "C" int fvlbm_plan_info(const fvlbm_mesh* mesh, const fvlbm_params* params, int32_t n_params,
+                               fvlbm_plan_info_t* info) {
+    clear_error();
+    if (!mesh || !info) return fail(FVLBM_ERR_ARG, "fvlbm_plan_info: null argument");
+    int rc = check_params(mesh->m, params, n_params);
+    if (rc) return rc;
+    Layout L;
+    try {
+        rc = make_layout(mesh->m, params[0].precision, params[0].scheme, params[0].kernel, L,
+                         device_sms(params[0].device), true);
+    } catch (const std::bad_alloc&) {
+        return fail(FVLBM_ERR_OOM, "fvlbm_plan_info: out of host memory");
+    }
+    if (rc) return rc;
+    const TilePlan& P = L.tp;
+    fvlbm_plan_info_t o{};
+    const bool tiled = L.strategy == STRATEGY_TILE;
+    o.stage_kernel = tiled ? P.tile : 1;
+    o.slots = L.maxf;
+    o.n_tiles = tiled ? P.n_tiles : 0;
+    o.short_tiles = P.short_tiles;
+    o.max_local_cells = P.max_local;
+    o.max_faces = P.max_faces;
+    if (tiled && P.n_tiles > 0) {
+        o.mean_tile_cells = (double)P.sum_len / P.n_tiles;
+        o.mean_ring1_cells = (double)P.sum_ring1 / P.n_tiles;
+        o.mean_local_cells = (double)P.sum_local / P.n_tiles;
+        o.face_table_waves = P.face_groups > 0 ? P.face_waves / P.face_groups : 0;
+        o.gather_waves = P.gather_groups > 0 ? P.gather_waves / P.gather_groups : 0;
+    }
+    o.violations = P.violations;
+    *info = o;
+    if (P.violations) fail(FVLBM_OK, "%lld failed plan checks; first: %s", (long long)P.violations,
+                           P.first_violation.c_str());
     return FVLBM_OK;
 }
 

@@ -57,6 +57,14 @@ class PartInfoT(C.Structure):
                 ("n_recv", C.c_int64), ("n_send", C.c_int64), ("n_neighbours", C.c_int32)]
 
 
+class PlanInfoT(C.Structure):
+    _fields_ = [("stage_kernel", C.c_int32), ("slots", C.c_int32), ("n_tiles", C.c_int64),
+                ("short_tiles", C.c_int64), ("max_local_cells", C.c_int32), ("max_faces", C.c_int32),
+                ("mean_tile_cells", C.c_double), ("mean_ring1_cells", C.c_double),
+                ("mean_local_cells", C.c_double), ("face_table_waves", C.c_double),
+                ("gather_waves", C.c_double), ("violations", C.c_int64)]
+
+
 class ServerConfigT(C.Structure):
     _fields_ = [("device", C.c_int32), ("n_streams", C.c_int32), ("arena_bytes", C.c_size_t),
                 ("max_active", C.c_int32), ("check_interval", C.c_int32), ("residual_tol", C.c_double),
@@ -76,7 +84,7 @@ class ServerStatsT(C.Structure):
 
 #: every symbol include/fvlbm.h declares
 EXPORTS = ["fvlbm_mesh_create", "fvlbm_mesh_concat", "fvlbm_mesh_destroy", "fvlbm_mesh_info",
-           "fvlbm_suggest_dt", "fvlbm_workspace_bytes", "fvlbm_init", "fvlbm_step", "fvlbm_macros",
+           "fvlbm_suggest_dt", "fvlbm_workspace_bytes", "fvlbm_plan_info", "fvlbm_init", "fvlbm_step", "fvlbm_macros",
            "fvlbm_residual", "fvlbm_mass", "fvlbm_mass_noalloc", "fvlbm_get_f", "fvlbm_set_f", "fvlbm_host_transfer", "fvlbm_stage_kernel", "fvlbm_sync",
            "fvlbm_get_dt", "fvlbm_profile", "fvlbm_autotune", "fvlbm_fma_peak", "fvlbm_launches_per_step", "fvlbm_solver_destroy",
            "fvlbm_server_create", "fvlbm_server_submit", "fvlbm_server_poll", "fvlbm_server_request",
@@ -105,6 +113,7 @@ def _load():
         "fvlbm_mesh_info": [P, C.POINTER(MeshInfoT)],
         "fvlbm_suggest_dt": [P, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_int32, dp],
         "fvlbm_workspace_bytes": [P, C.POINTER(ParamsT), C.c_int32, C.POINTER(C.c_size_t)],
+        "fvlbm_plan_info": [P, C.POINTER(ParamsT), C.c_int32, C.POINTER(PlanInfoT)],
         "fvlbm_init": [P, C.POINTER(ParamsT), C.c_int32, P, P, C.c_size_t, PP],
         "fvlbm_step": [P, C.c_int64],
         "fvlbm_macros": [P, dp, dp],
@@ -382,6 +391,20 @@ def fma_peak(device: int = 0, fp64: bool = True) -> float:
     t = C.c_double()
     _check(lib.fvlbm_fma_peak(device, 1 if fp64 else 0, C.byref(t)))
     return t.value
+
+
+def plan_info(mesh: Mesh, params) -> dict:
+    """The stage plan fvlbm_init would build, checked on the host (no GPU):
+    tile statistics, modelled shared-memory wavefronts, failed checks (and,
+    if any, the first one's description under "first_violation")."""
+    plist = [params] if isinstance(params, ParamsT) else list(params)
+    arr = (ParamsT * len(plist))(*plist)
+    i = PlanInfoT()
+    _check(lib.fvlbm_plan_info(mesh._h, arr, len(plist), C.byref(i)))
+    out = {k: getattr(i, k) for k, _ in PlanInfoT._fields_}
+    if out["violations"]:
+        out["first_violation"] = (lib.fvlbm_last_error() or b"").decode()
+    return out
 
 
 def autotune(mesh: Mesh, params, steps: int = 10, stream=None):

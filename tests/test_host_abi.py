@@ -130,3 +130,36 @@ def test_stage_kernel_capacity_on_the_host(fv):
     assert ws(hexes, "fp64", 1024)[0] == "UNSUPPORTED"
     assert ws(hexes, "fp32", 1024)[0] == "OK"
     assert ws(quads, "fp32", 384)[0] == "ARG"
+
+
+@pytest.mark.parametrize("name,make", [
+    ("cavity", lambda: mg.cavity(96, 20.0)),
+    ("cylinder", lambda: mg.cylinder_hybrid(n_rad=25, n_circ=50, n_tri_rings=25, seed=3)),
+    ("periodic", lambda: mg.periodic_tri(40, 30, lx=40.0, ly=30.0)),
+    ("bricks", lambda: mg.bricks(30, 20)),
+    ("couette", lambda: mg.couette()),
+])
+def test_tile_plan_checks(fv, name, make):
+    """The fused stage's tile plan, built and checked on the host: local links,
+    one face row per face, one writer per (face, direction), tiles within
+    their CTA; the bank-aware face rows keep the modelled face-table
+    wavefronts well below those of the neighbour gathers."""
+    m = make()
+    h = fv.Mesh(m)
+    for k in (128, 256, 512, 1024):
+        for prec in ("fp32", "fp16", "fp64"):
+            p = fv.make_params(0.1, scheme="rk2", precision=prec, kernel=k)
+            if prec == "fp64" and k == 1024:
+                with pytest.raises(fv.FvlbmError):
+                    fv.plan_info(h, p)
+                continue
+            i = fv.plan_info(h, p)
+            assert i["violations"] == 0, (name, k, prec, i.get("first_violation"))
+            assert i["stage_kernel"] == k and i["n_tiles"] >= 1
+            assert i["n_tiles"] * i["mean_tile_cells"] == pytest.approx(m.n_cell)
+            assert i["mean_tile_cells"] + i["mean_ring1_cells"] <= k
+            assert i["mean_local_cells"] <= i["max_local_cells"] <= 3 * k // 2 + 64
+            assert 1.0 <= i["face_table_waves"] < 1.8
+            assert 1.0 <= i["gather_waves"] < 2.6
+    two = fv.plan_info(h, fv.make_params(0.1, scheme="rk2", precision="fp64", kernel=1))
+    assert two["stage_kernel"] == 1 and two["n_tiles"] == 0 and two["violations"] == 0
