@@ -124,10 +124,12 @@ template <> struct CellIO<float> : PlainIO<float> {};
 // random integer below one 16-bit step, in units of q's last FP32 bit, is
 // added to q's magnitude and the sum is truncated (rounded toward zero) to the
 // 16-bit grid, which rounds up exactly when the random number reaches the
-// step minus q's remainder.  That holds for every finite FP32 value in BF16
-// (16 dropped bits, the same exponent range) and for FP16 normals (13 dropped
-// bits); below 2^-14, where FP16's grid spacing is fixed at 2^-24, the two
-// neighbours are compared with the random fraction instead.
+// step minus q's remainder.  BF16 (the same exponent range as FP32) drops 16
+// bits of every finite FP32 value.  FP16 adds, with one fused multiply-add, a
+// uniform fraction of the grid step at |q| (2^(e - 10) for FP16 normals,
+// 2^-24 for its subnormals below 2^-14), whose FP32 sum keeps the same ~13
+// random bits, and rounds toward zero: one formula for every magnitude, no
+// branch.
 // The random word of a cell comes from one integer hash of the bits of its
 // six rounded values (the "lowbias32" mixing function of C. Wellons'
 // hash-prospector, two multiply-xorshift rounds), spread over the directions
@@ -146,13 +148,13 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
 __device__ __forceinline__ uint32_t sr_word(uint32_t h, int a) { return h * (0x9E3779B9u + 2u * (uint32_t)a); }
 template <typename H> __device__ __forceinline__ uint32_t h_bits_sr(float q, uint32_t rnd);
 template <> __device__ __forceinline__ uint32_t h_bits_sr<__half>(float q, uint32_t rnd) {
-    const uint32_t b = __float_as_uint(q);
-    if ((b & 0x7F800000u) >= (113u << 23))   // |q| >= 2^-14: FP16 normal, 13 dropped bits
-        return __half_as_ushort(__float2half_rz(__uint_as_float(b + (rnd >> 19))));
-    const __half lo = __float2half_rd(q), hi = __float2half_ru(q);
-    const float flo = __half2float(lo), fhi = __half2float(hi);
-    return (float)(rnd >> 8) * (1.0f / 16777216.0f) * (fhi - flo) < q - flo ? __half_as_ushort(hi)
-                                                                             : __half_as_ushort(lo);
+    const uint32_t b = __float_as_uint(q), mag = b & 0x7FFFFFFFu;
+    // FP16 grid step at |q|: 2^(e - 10) for normals, 2^-24 below 2^-14 (subnormals)
+    const int e = max((int)(mag >> 23) - 127, -14);
+    const float step = __uint_as_float((uint32_t)(e - 10 + 127) << 23);
+    const float u = __uint_as_float(0x3F800000u | (rnd >> 9)) - 1.0f;   // uniform in [0, 1)
+    const float up = fmaf(u, step, __uint_as_float(mag));
+    return __half_as_ushort(__float2half_rz(__uint_as_float(__float_as_uint(up) | (b & 0x80000000u))));
 }
 template <> __device__ __forceinline__ uint32_t h_bits_sr<__nv_bfloat16>(float q, uint32_t rnd) {
     return (__float_as_uint(q) + (rnd >> 16)) >> 16;
