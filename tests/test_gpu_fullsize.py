@@ -35,10 +35,11 @@ def _offsets(variants, inst):
 
 
 # measured maxima over the picks after 20 steps: FP32 2.6e-7, FP64 1.7e-14,
-# FP16 split 1.0e-3, BF16 split 1.2e-2 (a low-Re cavity just after its impulsive
-# start; the non-equilibrium part is stored in 16 bits, 11 significant bits in
-# FP16, 8 in BF16, with unbiased rounding: zero-mean noise that shows first,
-# where round-to-nearest showed a bias that grew instead)
+# FP16 split 1.0e-3, BF16 split 1.2e-2 (a low-Re cavity, where tau / dt is
+# large: the non-equilibrium part is stored in 16 bits, 11 significant bits in
+# FP16, 8 in BF16, with unbiased rounding, and its zero-mean noise accumulates
+# over the tau / dt steps n takes to relax; round to nearest showed a bias that
+# grew instead)
 @pytest.mark.parametrize("prec,kernel,tol", [("fp32", 512, 2e-6), ("fp64", 1, 1e-12), ("fp16", 512, 2e-3),
                                              ("bf16", 512, 2e-2)])
 def test_full_batch_sampled_instances_match_oracle(fv, orc, batch, prec, kernel, tol):
