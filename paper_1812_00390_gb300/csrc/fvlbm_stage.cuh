@@ -454,8 +454,9 @@ __device__ __forceinline__ void tile_gradient_faces(const uint2* dx, const Geo& 
 // and 1-ring together at most TILE cells), everything between the state read
 // and the state write in shared memory:
 //   phase 1  cp.async of the state of the tile, its 1-ring and its 2-ring
-//            (the 16-bit formats raw, decoded after the barrier) and of the
-//            instance id of each tile cell; the slot descriptors and the
+//            (the 16-bit formats raw, each cell decoded by the thread that
+//            staged it) and of the instance id of each tile cell; the slot
+//            descriptors and the
 //            least-squares vectors of each thread's gradient cell into
 //            registers
 //   phase 2  per tile and 1-ring cell (one per thread): the gradient
@@ -469,12 +470,12 @@ __device__ __forceinline__ void tile_gradient_faces(const uint2* dx, const Geo& 
 // The global loads of each phase are issued before the barrier that precedes
 // it, so that their latency overlaps the wait, and each CTA prefetches into L2
 // the data of a tile that starts somewhat under one CTA lifetime later (pf =
-// 5/8 of the resident CTAs ahead).  The kernel is bound by shared-memory traffic more than by
-// DRAM: what a thread can hold in registers (its own state, its least-squares
-// vectors) or read through L1 (reconstruction and face vectors) stays out of
-// shared memory, whose small footprint leaves L1 large.  Shared-memory
-// strides are compile-time constants (TileDims); the planner keeps every tile
-// within them.
+// 5/8 of the resident CTAs ahead).  The kernel is bound by shared-memory
+// traffic more than by DRAM: what a thread can hold in registers (its own
+// state, its least-squares vectors) or read through L1 (reconstruction and
+// face vectors) stays out of shared memory, whose small footprint leaves L1
+// large.  Shared-memory strides are compile-time constants (TileDims); the
+// planner keeps every tile within them.
 template <typename T, typename S, int MAXF, bool DEV, int TILE>
 __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0 ? (sizeof(T) == 4 ? 1024 : 512) / TILE : 1)
     stage_tile_kernel(DevView v, const S* __restrict__ fin, const S* fbase, S* fout, T beta, int mode, int pf) {
@@ -500,8 +501,8 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
 
     // phase 1 (thread l's first local cell is local cell l).  The 16-bit split
     // formats are staged raw (moments, packed non-equilibrium words, instance)
-    // in the face-table area, which is free until phase 2, and decoded after
-    // the barrier.
+    // in the face-table area, which is free until phase 2, and decoded by the
+    // thread that staged them.
     constexpr bool PLAIN = sizeof(S) == sizeof(T);
     float* rawc = (float*)fvs;                     // [3][LS]
     uint32_t* raww = (uint32_t*)(rawc + 3 * LS);   // [3][LS]
@@ -549,9 +550,8 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 1024 : 512) / TILE > 0
     // A CTA that starts somewhat before this one ends works on about tile
     // t + pf (pf = 5/8 of the CTAs resident on the GPU): bring that tile's
     // state and geometry into L2 now, so that its staging reads L2 rather than
-    // HBM.  The last thread does
-    // it once its own copies are in flight, so that the loads of the other
-    // tile's bounds overlap them.
+    // HBM.  The last thread does it once its own copies are in flight, so that
+    // the loads of the other tile's bounds overlap them.
     if (l == TILE - 1 && pf > 0 && t + pf < v.n_tiles) {
         const int64_t tp = t + pf;
         const int64_t b0 = v.tile_begin[tp] >> BLK_SHIFT;
