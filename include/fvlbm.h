@@ -499,9 +499,13 @@ int fvlbm_partition_halo(const fvlbm_partition* p, int32_t src, int32_t dst, int
 
 /*
  * A partitioned solve on one GPU: one solver per part (each with its own
- * workspace, allocated by the library), all on one stream, with the halo
- * exchange after every stage as a device-to-device copy of the ghost states
- * (one kernel over all messages).  The FP64 reductions (mass, residual) sum
+ * workspace, allocated by the library); with more than one part each part's
+ * stages run on a stream of its own (so that the parts' kernels overlap), and
+ * the halo exchange after every stage, a device-to-device copy of the ghost
+ * states (one kernel over all messages), runs on the caller's stream after
+ * every part's stage and before any part's next (events order them).  Work
+ * the caller queued on its stream before fvlbm_dd_step runs first; the
+ * caller's stream holds the last exchange of a step.  The FP64 reductions (mass, residual) sum
  * the parts' FP64 partial sums in part order.  A multi-GPU run would place
  * one part per GPU and carry the same messages over the interconnect; this
  * library runs all parts on the device of params->device.

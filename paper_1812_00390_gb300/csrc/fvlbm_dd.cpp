@@ -17,7 +17,12 @@ struct fvlbm_dd {
     std::vector<fvlbm_solver*> part;
     int device = 0;
     int prec = FVLBM_FP64;
-    void* stream = nullptr;
+    void* stream = nullptr;   // the caller's: the halo exchange, and the order every call keeps
+    // with more than one part, each part's stages run on a stream of its own,
+    // so that the parts' kernels overlap; events order them with the exchange
+    std::vector<cudaStream_t> part_stream;
+    std::vector<cudaEvent_t> part_done;
+    cudaEvent_t main_done = nullptr;
     int4* entries = nullptr;   // device: (src part, src internal cell, dst part, dst internal cell)
     int64_t n_entries = 0;
 };
@@ -26,9 +31,31 @@ namespace {
 
 int cuda_fail(cudaError_t e, const char* what) { return fail(FVLBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e)); }
 
-// Copy every ghost's state from its owner, each part's buffer given.
+// The parts' streams wait for the work queued on the caller's stream.
+int fork(fvlbm_dd* d) {
+    if (d->part_stream.empty()) return FVLBM_OK;
+    cudaError_t e = cudaEventRecord(d->main_done, (cudaStream_t)d->stream);
+    for (size_t p = 0; e == cudaSuccess && p < d->part_stream.size(); p++)
+        e = cudaStreamWaitEvent(d->part_stream[p], d->main_done, 0);
+    return e == cudaSuccess ? FVLBM_OK : cuda_fail(e, "partitioned solve: stream order");
+}
+
+// The caller's stream waits for the work queued on every part's stream.
+int join(fvlbm_dd* d) {
+    cudaError_t e = cudaSuccess;
+    for (size_t p = 0; e == cudaSuccess && p < d->part_stream.size(); p++) {
+        e = cudaEventRecord(d->part_done[p], d->part_stream[p]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent((cudaStream_t)d->stream, d->part_done[p], 0);
+    }
+    return e == cudaSuccess ? FVLBM_OK : cuda_fail(e, "partitioned solve: stream order");
+}
+
+// Copy every ghost's state from its owner, each part's buffer given: on the
+// caller's stream, after every part's queued work, and before any part's next.
 int exchange(fvlbm_dd* d, void* const* bufs) {
-    return launch_halo_copy(d->prec, d->stream, d->entries, d->n_entries, bufs, (int)d->part.size());
+    int rc = join(d);
+    if (!rc) rc = launch_halo_copy(d->prec, d->stream, d->entries, d->n_entries, bufs, (int)d->part.size());
+    return rc ? rc : fork(d);
 }
 
 // Exchange on the parts' current states.
@@ -48,9 +75,27 @@ int create_impl(fvlbm_dd* d, const fvlbm_partition* plan, const fvlbm_params* pa
     d->device = params->device;
     d->prec = params->precision;
     d->stream = stream;
+    {
+        DeviceGuard dg(d->device);
+        if (plan->n_parts > 1) {
+            cudaError_t e = cudaEventCreateWithFlags(&d->main_done, cudaEventDisableTiming);
+            for (int32_t p = 0; e == cudaSuccess && p < plan->n_parts; p++) {
+                cudaStream_t ps = nullptr;
+                cudaEvent_t pe = nullptr;
+                e = cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking);
+                if (e == cudaSuccess) d->part_stream.push_back(ps);
+                if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pe, cudaEventDisableTiming);
+                if (e == cudaSuccess) d->part_done.push_back(pe);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "fvlbm_dd_create: part streams");
+            int rc = fork(d);   // the parts start after the caller's queued work
+            if (rc) return rc;
+        }
+    }
     for (int32_t p = 0; p < plan->n_parts; p++) {
         fvlbm_solver* s = nullptr;
-        int rc = fvlbm_init(plan->parts[p].mesh, params, 1, stream, nullptr, 0, &s);
+        void* ps = d->part_stream.empty() ? stream : (void*)d->part_stream[p];
+        int rc = fvlbm_init(plan->parts[p].mesh, params, 1, ps, nullptr, 0, &s);
         if (rc) return rc;
         d->part.push_back(s);
     }
@@ -85,10 +130,11 @@ int create_impl(fvlbm_dd* d, const fvlbm_partition* plan, const fvlbm_params* pa
 extern "C" void fvlbm_dd_destroy(fvlbm_dd* d) {
     if (!d) return;
     for (fvlbm_solver* s : d->part) fvlbm_solver_destroy(s);
-    if (d->entries) {
-        DeviceGuard dg(d->device);
-        cudaFree(d->entries);
-    }
+    DeviceGuard dg(d->device);
+    if (d->entries) cudaFree(d->entries);
+    for (cudaStream_t ps : d->part_stream) cudaStreamDestroy(ps);
+    for (cudaEvent_t pe : d->part_done) cudaEventDestroy(pe);
+    if (d->main_done) cudaEventDestroy(d->main_done);
     delete d;
 }
 
@@ -119,6 +165,8 @@ extern "C" int fvlbm_dd_step(fvlbm_dd* d, int64_t n) {
     DeviceGuard dg(d->device);
     const int ns = solver_n_stages(d->part[0]);
     std::vector<void*> bufs(d->part.size());
+    int frc = fork(d);   // after the work the caller queued on its stream
+    if (frc) return frc;
     for (int64_t t = 0; t < n; t++)
         for (int k = 0; k < ns; k++) {
             for (size_t p = 0; p < d->part.size(); p++) {
@@ -138,7 +186,9 @@ extern "C" int fvlbm_dd_sync(fvlbm_dd* d) {
         int rc = fvlbm_sync(s);
         if (rc) return rc;
     }
-    return FVLBM_OK;
+    DeviceGuard dg(d->device);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)d->stream);
+    return e == cudaSuccess ? FVLBM_OK : cuda_fail(e, "fvlbm_dd_sync");
 }
 
 namespace {
